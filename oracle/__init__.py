@@ -55,6 +55,8 @@ def _load():
         lib.or_cs_row_sumsq.argtypes = [c_int, u64, vp, vp]
         lib.or_cs_f2.argtypes = [c_int, u64, vp, vp]
         lib.or_cs_x_many.argtypes = [c_int, u64, c_int, u64, c_int, vp, u64, vp, c_int, vp, u64, vp]
+        lib.or_cs_point_query.argtypes = [c_int, u64, c_int, c_int, u64, c_int, vp, vp, vp, c_int,
+                                          u64, vp]
         lib.or_divmod.argtypes = [c_int, u64, vp, u64, vp, vp]
         lib.or_exact_f2.argtypes = [vp, vp, u64, vp]
         _lib = lib
@@ -190,6 +192,19 @@ def cs_x_many(b: int, c: int, k: int, m: int, mode: int, coeffs: np.ndarray, key
     out = np.empty((nsets, 2), dtype=np.uint64)
     _load().or_cs_x_many(b, c, k, m, mode, coeffs.ctypes.data, nsets, keys.ctypes.data, kind,
                          _ptr(weights), n, out.ctypes.data)
+    return out
+
+
+def point_query(b: int, c: int, k: int, mode: int, coeffs: np.ndarray, counters: np.ndarray,
+                keys: np.ndarray) -> np.ndarray:
+    """Median over rows of s_r(x) C[r][i_r(x)] for each key (int64)."""
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.uint64).reshape(-1, 2)
+    counters = np.ascontiguousarray(counters, dtype=np.int64)
+    t, m = counters.shape
+    keys, kind, n = _keys(keys)
+    out = np.empty(n, dtype=np.int64)
+    _load().or_cs_point_query(b, c, k, t, m, mode, coeffs.ctypes.data, counters.ctypes.data,
+                              keys.ctypes.data, kind, n, out.ctypes.data)
     return out
 
 

@@ -31,6 +31,8 @@
  *  - or_divmod:    floor(v / p) and v mod p for 128-bit v (what Algorithms
  *                  div-simple, division-generalized and mod-generalized of
  *                  Sec. 1.6 compute), by the C operators.
+ *  - or_cs_point_query: the point-query estimate of f_x, median over rows of
+ *                  s_r(x) C[r][i_r(x)] (Sec. 1.4, estimating a single value).
  *  - or_exact_f2:  F2 = sum_x f_x^2 of a weighted stream (Sec. 1.4 setup).
  *
  * Conventions shared with the library's contract (not its code): counters are
@@ -288,6 +290,38 @@ void or_cs_x_many(int b, u64 c, int k, u64 m, int two_poly, const u64* coeff_pai
         or_cs_row_sumsq(1, m, C, x_pairs + 2 * s);
     }
     free(C);
+}
+
+/* Point query (Sec. 1.4): the estimate of f_x is the median over the t rows of
+ * s_r(x) * C[r][i_r(x)] (t odd: the middle value after sorting). */
+void or_cs_point_query(int b, u64 c, int k, int t, u64 m, int two_poly, const u64* coeff_pairs,
+                       const int64_t* C, const void* keys, int key_kind, u64 n, int64_t* out) {
+    u128 p = or_prime(b, c);
+    int nf = two_poly ? 2 : 1;
+    u128* a = (u128*)malloc(sizeof(u128) * (size_t)t * (size_t)nf * (size_t)k);
+    int64_t* est = (int64_t*)malloc(sizeof(int64_t) * (size_t)t);
+    for (int f = 0; f < t * nf; ++f) or_load_coeffs(coeff_pairs + 2 * (u64)f * (u64)k, k, a + f * k);
+    for (u64 j = 0; j < n; ++j) {
+        u128 x = or_key(keys, key_kind, j);
+        for (int r = 0; r < t; ++r) {
+            const u128* ab = a + (size_t)(r * nf) * k;
+            const u128* as = two_poly ? ab + k : ab;
+            u64 bucket;
+            int sign;
+            or_split(p, b, k, m, two_poly, ab, as, x, &bucket, &sign);
+            u64 cv = (u64)C[(u64)r * m + bucket];
+            est[r] = (int64_t)(sign > 0 ? cv : (u64)0 - cv);
+        }
+        for (int i = 1; i < t; ++i) {
+            int64_t v = est[i];
+            int q = i - 1;
+            while (q >= 0 && est[q] > v) { est[q + 1] = est[q]; --q; }
+            est[q + 1] = v;
+        }
+        out[j] = est[t / 2];
+    }
+    free(est);
+    free(a);
 }
 
 /* ---------------- division and modulus ---------------- */

@@ -426,3 +426,31 @@ def test_exact_f2_small():
     w = np.array([1, 2, -4, 10, -3, -2], dtype=np.int32)
     assert oracle.exact_f2(keys, w) == 7 * 7 + 0 + 9
     assert oracle.exact_f2(keys) == 9 + 4 + 1
+
+
+def test_point_query_definition():
+    """Point query (Sec. 1.4): with h(x) = x in every row (injective buckets for
+    keys < m) each row's estimate s(x) C[i(x)] is exactly f_x, so the median is
+    f_x; a key sharing its bucket with nothing else reads back its own weight."""
+    n, m, t = 100, 128, 3
+    coeffs = oracle.from_ints([0, 1] * t)
+    keys = np.arange(n, dtype=np.uint64)
+    w = datagen.i32_range(3, -100, 100, n)
+    C = oracle.cs_update(61, 1, 2, t, m, oracle.TWO_FOR_ONE, coeffs, keys, w)
+    assert (oracle.point_query(61, 1, 2, oracle.TWO_FOR_ONE, coeffs, C, keys) == w).all()
+    # h(x) = 2^60 + x has sign bit 1: the counters hold -f_x and the query returns f_x
+    coeffs = oracle.from_ints([1 << 60, 1] * t)
+    C = oracle.cs_update(61, 1, 2, t, m, oracle.TWO_FOR_ONE, coeffs, keys, w)
+    assert (C[:, :n] == -w).all()
+    assert (oracle.point_query(61, 1, 2, oracle.TWO_FOR_ONE, coeffs, C, keys) == w).all()
+
+
+def test_point_query_median_of_rows():
+    """Rows disagree: the median (not the mean or the first row) is returned."""
+    t, m = 3, 8
+    # row r hashes every key to the constant bucket r, sign +
+    coeffs = oracle.from_ints([0, 0, 1, 0, 2, 0])
+    C = np.array([[5, 0, 0, 0, 0, 0, 0, 0], [0, -7, 0, 0, 0, 0, 0, 0], [0, 0, 40, 0, 0, 0, 0, 0]],
+                 dtype=np.int64)
+    assert list(oracle.point_query(61, 1, 2, oracle.TWO_FOR_ONE, coeffs, C,
+                                   np.array([9, 10], dtype=np.uint64))) == [5, 5]
