@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Benchmark: Count Sketch key updates/s (k=4, p=2^61-1) on GB300.
+
+Default workload (one JSON line): the large single sketch -- 2^28 keys drawn
+Zipf(1.1) over a universe of 2^32 mapped to 61-bit keys, unit weights, t=7
+rows, m=2^16 counters per row (3.5 MiB of int64 counters), two-for-one
+hashing.  One step = zero the counters, cs_update over the whole stream,
+cs_estimate_f2 (every step of the path, in the library's kernels).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload large|large-twopoly|plain|plain-2^28|sweep|batched]
+
+`value` is whole-job keys/s with the keys already resident in HBM (2 GiB per
+rank, far larger than the 129 MB L2, so no flush is needed between steps).
+`e2e` is the same metric through the C ABI from pinned host buffers: each step
+copies its keys host->device, updates, estimates F2 and reads the 16-byte
+estimate back.  `roofline` is for the dominant kernel (k_cs_update), timed by
+CUDA events on its own stream.  `cpu_baseline` (rank 0, N=1) times the CPU
+oracle on a bounded sample of the same stream on this host's cores.
+--impl reference times the CPU oracle alone (this method has no other
+reference implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import datagen  # noqa: E402
+
+P61 = (1 << 61) - 1
+
+WORKLOADS = {
+    # name: (n, t, m, mode, keys, weights)
+    "large": dict(n=1 << 28, t=7, m=1 << 16, mode=0, keys="zipf", weights=None,
+                  desc="large single sketch: 2^28 Zipf(1.1) keys over 2^32, unit weights, "
+                       "t=7, m=2^16, two-for-one"),
+    "large-twopoly": dict(n=1 << 28, t=7, m=1 << 16, mode=1, keys="zipf", weights=None,
+                          desc="large single sketch, two polynomials per row"),
+    "plain": dict(n=1 << 20, t=5, m=1024, mode=0, keys="uniform", weights="pm100",
+                  desc="plain single sketch: 2^20 uniform keys < 2^61-1, int32 weights in "
+                       "[-100,100], t=5, m=1024"),
+    "plain-2^28": dict(n=1 << 28, t=5, m=1024, mode=0, keys="uniform", weights="pm100",
+                       desc="plain sketch distribution at 2^28 keys"),
+}
+
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=2008)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ inputs
+
+def make_inputs(wl: dict, seed: int, rank: int, n: int | None = None):
+    n = wl["n"] if n is None else n
+    s = seed + 1000003 * rank
+    if wl["keys"] == "zipf":
+        keys = datagen.zipf(s, 1.1, 1 << 32, n)
+    else:
+        keys = datagen.u64_below(s, P61, n)
+    w = datagen.i32_range(s, -100, 100, n) if wl["weights"] == "pm100" else None
+    return keys, w
+
+
+def inputs_desc(wl: dict) -> str:
+    k = ("Zipf(1.1) ranks over [1,2^32] by rejection-inversion, rank r -> key "
+         "r*0x9E3779B97F4A7C15 mod 2^61" if wl["keys"] == "zipf"
+         else "uniform below 2^61-1 (SplitMix64 words scaled by p)")
+    w = "unit weights" if wl["weights"] is None else "int32 weights uniform in [-100,100]"
+    return "%s; %s; seeded counter-based generator (datagen)" % (k, w)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            self.path = "/tmp/ms_bench_clocks_%d.csv" % os.getpid()
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + CLOCK_QUERY, "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ cpu baseline
+
+def cpu_baseline(wl: dict, seed: int, target_s: float, gpu_check=None) -> dict:
+    """The CPU oracle on a bounded sample of the same stream, all host cores."""
+    import oracle
+    cores = os.cpu_count() or 1
+    coeffs = oracle.sketch_coeffs(61, 1, 4, wl["t"], wl["mode"], seed)
+    n_cal = 1 << 16
+    keys, w = make_inputs(wl, seed, 0, n_cal)
+    t0 = time.perf_counter()
+    oracle.cs_update(61, 1, 4, wl["t"], wl["m"], wl["mode"], coeffs, keys, w, nthreads=cores)
+    rate = n_cal / max(time.perf_counter() - t0, 1e-6)
+    n = int(min(wl["n"], max(1 << 16, rate * target_s)))
+    n = 1 << int(math.log2(n))
+    keys, w = make_inputs(wl, seed, 0, n)
+    t0 = time.perf_counter()
+    C = oracle.cs_update(61, 1, 4, wl["t"], wl["m"], wl["mode"], coeffs, keys, w, nthreads=cores)
+    f2 = oracle.f2_estimate(C)
+    dt = time.perf_counter() - t0
+    out = {"value": n / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
+           "sample": "first %d keys of the same seeded stream (%.1f s of CPU time on %d threads)"
+                     % (n, dt, cores)}
+    if gpu_check is not None:
+        out["parity_on_sample"] = bool(gpu_check(keys, w, C, f2))
+    return out
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2008_08654_gb300 as ms
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    n, t, m, mode = wl["n"], wl["t"], wl["m"], wl["mode"]
+    keys_np, w_np = make_inputs(wl, args.seed, rank)
+    keys = torch.from_numpy(keys_np.view(np.int64)).to(dev)
+    w = None if w_np is None else torch.from_numpy(w_np).to(dev)
+    sk = ms.Sketch(t=t, m=m, k=4, b=61, c=1, seed=args.seed, mode=mode)
+    f2_out = torch.empty(2, dtype=torch.int64, device=dev)
+
+    def step():
+        sk.reset()
+        sk.update(keys, w)
+        sk.estimate_f2(out=f2_out)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    launch = sk.last_launch()
+
+    # device-timed steps, with per-step events around the update kernel
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        sk.reset()
+        ev[i][0].record(stream)
+        sk.update(keys, w)
+        ev[i][1].record(stream)
+        sk.estimate_f2(out=f2_out)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    kern_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    f2_est = ms.u128_to_int(f2_out.cpu())
+
+    # e2e through the C ABI from pinned host buffers (copies in the timed region)
+    keys_h = torch.from_numpy(keys_np.view(np.int64)).pin_memory()
+    w_h = None if w_np is None else torch.from_numpy(w_np).pin_memory()
+    keys_d = torch.empty_like(keys)
+    w_d = None if w is None else torch.empty_like(w)
+    f2_h = torch.empty(2, dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+
+    def e2e_step():
+        keys_d.copy_(keys_h, non_blocking=True)
+        if w_d is not None:
+            w_d.copy_(w_h, non_blocking=True)
+        sk.reset()
+        sk.update(keys_d, w_d)
+        sk.estimate_f2(out=f2_out)
+        f2_h.copy_(f2_out, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    assert ms.u128_to_int(f2_h) == f2_est
+
+    # integer-multiply peak on this GPU (the roofline's denominator)
+    imad_rate, _ = ms.probe_mul128(variant=1, iters=1 << 14)
+    mul_rate, _ = ms.probe_mul128(variant=0, iters=1 << 12)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+
+    value = world * n * args.steps / (ms_total * 1e-3)
+    kern_avg_s = statistics.mean(kern_ms) * 1e-3
+    mul128_per_key = t * 3 * (2 if mode == 1 else 1)
+    achieved_mul = n * mul128_per_key / kern_avg_s
+    peak_mul = imad_rate / 4.0  # 4 32x32->64 partial products per 64x64 product
+    bytes_per_key = 8 + (4 if w is not None else 0)
+    hbm_peak = 6787.9
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        pass
+    line = {
+        "metric": "Count Sketch key updates/s (k=4, p=2^61-1)",
+        "value": value,
+        "unit": "keys/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": ms_total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "keys_per_step_per_gpu": n, "t": t, "m": m, "k": 4,
+                   "p": "2^61-1", "mode": "two-poly" if mode == 1 else "two-for-one",
+                   "inputs": inputs_desc(wl), "seed": args.seed,
+                   "l2": "inputs (%d MiB per GPU) exceed the 129 MB L2; no flush" %
+                         (n * bytes_per_key >> 20),
+                   "launch": launch, "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {
+            "bound": "alu",
+            "achieved": achieved_mul / 1e9,
+            "peak": peak_mul / 1e9,
+            "unit": "Gmul128/s",
+            "frac": achieved_mul / peak_mul,
+            "traffic": None,
+            "kernel": "k_cs_update",
+            "kernel_ms": statistics.mean(kern_ms),
+            "mul128_per_key": mul128_per_key,
+            "peak_source": "ms_probe_mul128 variant 1 (independent 32x32->64 multiply-adds on "
+                           "every SM, measured in this run) / 4 partial products per 64x64 product",
+            "probe_mul64x64_per_s": mul_rate,
+            "hbm": {"achieved_gbs": n * bytes_per_key / kern_avg_s / 1e9, "peak_gbs": hbm_peak,
+                    "frac": n * bytes_per_key / kern_avg_s / 1e9 / hbm_peak},
+        },
+        "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": "keys/s",
+                "h2d_bytes_per_step": n * bytes_per_key, "d2h_bytes_per_step": 16},
+        "gpu_launches": 3 * args.steps,
+        "f2_estimate": str(f2_est),
+    }
+    if clk:
+        line["clocks"] = clk
+    if world == 1 and not args.no_cpu_baseline:
+        def gpu_check(kn, wn, C_oracle, f2_oracle):
+            s2 = ms.Sketch(t=t, m=m, k=4, b=61, c=1, seed=args.seed, mode=mode)
+            s2.update(torch.from_numpy(kn.view(np.int64)).to(dev),
+                      None if wn is None else torch.from_numpy(wn).to(dev))
+            return (np.array_equal(s2.counters().cpu().numpy(), C_oracle)
+                    and s2.f2() == f2_oracle)
+        line["cpu_baseline"] = cpu_baseline(wl, args.seed, args.cpu_seconds, gpu_check)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, wl):
+    """The CPU oracle timed as the reference arm: K timed steps, each the oracle
+    over the same bounded sample of the workload's stream (all host cores),
+    sized so that the whole run takes about a minute and a half."""
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    cores = os.cpu_count() or 1
+    coeffs = oracle.sketch_coeffs(61, 1, 4, wl["t"], wl["mode"], args.seed)
+    kc, wc = make_inputs(wl, args.seed, 0, 1 << 16)
+    t0 = time.perf_counter()
+    oracle.cs_update(61, 1, 4, wl["t"], wl["m"], wl["mode"], coeffs, kc, wc, nthreads=cores)
+    rate = (1 << 16) / max(time.perf_counter() - t0, 1e-6)
+    per_step = max(0.05, min(args.cpu_seconds, 90.0 / max(1, args.steps)))
+    n = int(min(wl["n"], max(1 << 12, rate * per_step)))
+    n = 1 << int(math.log2(n))
+    keys, w = make_inputs(wl, args.seed, 0, n)
+    for _ in range(max(0, args.warmup)):
+        oracle.cs_update(61, 1, 4, wl["t"], wl["m"], wl["mode"], coeffs, keys[:4096],
+                         None if w is None else w[:4096], nthreads=cores)
+    total = 0.0
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        C = oracle.cs_update(61, 1, 4, wl["t"], wl["m"], wl["mode"], coeffs, keys, w,
+                             nthreads=cores)
+        oracle.f2_estimate(C)
+        total += time.perf_counter() - t0
+    steps = max(1, args.steps)
+    value = n * steps / total
+    sample = ("first %d keys of the same seeded stream per step, %d steps, %.1f s total on %d "
+              "threads" % (n, steps, total, cores))
+    return {
+        "impl": "reference",
+        "metric": "Count Sketch key updates/s (k=4, p=2^61-1)",
+        "value": value,
+        "unit": "keys/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": total / steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "inputs": inputs_desc(wl), "seed": args.seed},
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "note": "the method has no reference implementation; this arm is the plain CPU oracle "
+                "(unsigned __int128 % and /) on a bounded sample of the same stream",
+    }
+
+
+def main():
+    args = parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        line = run_reference(args, wl)
+    else:
+        line = run_ours(args, wl)
+    if line is not None:
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(s + "\n")
+
+
+if __name__ == "__main__":
+    main()

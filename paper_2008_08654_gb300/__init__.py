@@ -1,0 +1,366 @@
+"""Python binding of libms, the GB300 (sm_103a) Mersenne-prime hashing and
+Count Sketch library (include/ms.h).
+
+The binding only marshals arguments: every computation runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if libms.so is missing or a call fails, an exception is raised.
+
+Names follow the C ABI: hash_init / Hash.eval (ms_hash_*), div / mod
+(ms_div / ms_mod), Sketch (cs_*), probe_mul128 (ms_probe_mul128).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libms.so")
+
+TWO_FOR_ONE = 0
+TWO_POLY = 1
+
+PLACE_SMEM, PLACE_DSMEM, PLACE_GLOBAL = 0, 1, 2
+STRAT_HORNER, STRAT_POWER_SUM = 0, 1
+
+PRIMES = ((31, 1), (61, 1), (89, 1), (64, 59))
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported prime", 3: "value out of range",
+          4: "out of memory", 5: "CUDA error", 6: "timeout", 7: "busy", 8: "misaligned pointer"}
+
+
+class MSError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = "%s failed: %s" % (where, STATUS.get(status, "status %d" % status))
+        if detail:
+            msg += " (" + detail + ")"
+        super().__init__(msg)
+
+
+class U128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libms.so is not built (expected at %s); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, u32, u64, sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
+                           ctypes.c_size_t)
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    dbl = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    sigs = {
+        "ms_status_str": (ctypes.c_char_p, [i]),
+        "ms_last_cuda_error": (ctypes.c_char_p, []),
+        "ms_version": (ctypes.c_char_p, []),
+        "ms_hash_init": (i, [pp, i, i, u64, u64]),
+        "ms_hash_init_coeffs": (i, [pp, i, i, u64, vp]),
+        "ms_hash_coeffs": (i, [vp, vp]),
+        "ms_hash_params": (i, [vp, ip, ip, ctypes.POINTER(u64)]),
+        "ms_hash_eval": (i, [vp, vp, vp, sz, vp]),
+        "ms_hash_destroy": (i, [vp]),
+        "ms_div": (i, [i, u64, vp, vp, vp, sz, vp]),
+        "ms_mod": (i, [i, u64, vp, vp, sz, vp]),
+        "cs_create": (i, [pp, i, u32, i, i, u64, u64, i]),
+        "cs_create_coeffs": (i, [pp, i, u32, i, i, u64, i, vp]),
+        "cs_destroy": (i, [vp]),
+        "cs_params": (i, [vp, ip, ctypes.POINTER(u32), ip, ip, ctypes.POINTER(u64), ip]),
+        "cs_coeffs": (i, [vp, vp]),
+        "cs_update": (i, [vp, vp, vp, sz, vp]),
+        "cs_estimate_f2": (i, [vp, vp, vp, vp]),
+        "cs_point_query": (i, [vp, vp, vp, sz, vp]),
+        "cs_counters": (i, [vp, pp]),
+        "cs_reset": (i, [vp, vp]),
+        "cs_merge": (i, [vp, vp, vp]),
+        "cs_export": (i, [vp, vp, ctypes.POINTER(sz), vp]),
+        "cs_import": (i, [pp, vp, sz]),
+        "cs_set_launch": (i, [vp, i, i, i, i, i, i]),
+        "cs_last_launch": (i, [vp, ip, ip, ip, ip, ip, ip, ip]),
+        "ms_probe_mul128": (i, [i, i, vp, dbl, dbl]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lib():
+    """The loaded ctypes library (loads it on first use)."""
+    return _load()
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        detail = ""
+        if st == 5:
+            detail = _load().ms_last_cuda_error().decode(errors="replace")
+        raise MSError(st, where, detail)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor on a CUDA device")
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def key_dtype_bytes(b: int, c: int) -> int:
+    return {(31, 1): 4, (61, 1): 8, (89, 1): 16, (64, 59): 8}[(b, c)]
+
+
+def _nkeys(keys: torch.Tensor, b: int, c: int) -> int:
+    kb = key_dtype_bytes(b, c)
+    total = keys.numel() * keys.element_size()
+    if total % kb:
+        raise ValueError("key tensor size is not a multiple of the %d-byte key type" % kb)
+    return total // kb
+
+
+def _u128_array(values):
+    arr = (U128 * len(values))()
+    for j, v in enumerate(values):
+        v = int(v)
+        arr[j].lo = v & ((1 << 64) - 1)
+        arr[j].hi = (v >> 64) & ((1 << 64) - 1)
+    return arr
+
+
+def version() -> str:
+    return _load().ms_version().decode()
+
+
+# ------------------------------------------------------------------ hashing
+
+class Hash:
+    """h(x) = sum_{i<k} a_i x^i mod p (ms_hash_*)."""
+
+    def __init__(self, k: int = 4, b: int = 61, c: int = 1, seed: int = 0, coeffs=None):
+        lib_ = _load()
+        h = ctypes.c_void_p()
+        if coeffs is None:
+            _check(lib_.ms_hash_init(ctypes.byref(h), k, b, c, seed), "ms_hash_init")
+        else:
+            arr = _u128_array(coeffs)
+            _check(lib_.ms_hash_init_coeffs(ctypes.byref(h), len(coeffs), b, c, arr),
+                   "ms_hash_init_coeffs")
+            k = len(coeffs)
+        self._h = h
+        self.k, self.b, self.c = k, b, c
+
+    def coeffs(self) -> list:
+        arr = (U128 * self.k)()
+        _check(_load().ms_hash_coeffs(self._h, arr), "ms_hash_coeffs")
+        return [a.lo | (a.hi << 64) for a in arr]
+
+    def out_tensor(self, n: int, device=None) -> torch.Tensor:
+        device = device or torch.device("cuda")
+        if (self.b, self.c) == (31, 1):
+            return torch.empty(n, dtype=torch.int32, device=device)
+        if (self.b, self.c) == (89, 1):
+            return torch.empty((n, 2), dtype=torch.int64, device=device)
+        return torch.empty(n, dtype=torch.int64, device=device)
+
+    def eval(self, keys: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        n = _nkeys(keys, self.b, self.c)
+        if out is None:
+            out = self.out_tensor(n, keys.device)
+        _check(_load().ms_hash_eval(self._h, _ptr(keys), _ptr(out), n, _stream(stream)),
+               "ms_hash_eval")
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ms_hash_destroy(self._h)
+            self._h = None
+
+
+def hash_init(k: int, b: int = 61, c: int = 1, seed: int = 0) -> Hash:
+    return Hash(k, b, c, seed)
+
+
+# ------------------------------------------------------------------ division
+
+def div(b: int, c: int, v: torch.Tensor, q: torch.Tensor | None = None,
+        r: torch.Tensor | None = None, want_q: bool = True, want_r: bool = True, stream=None):
+    """q = v // p (as (n,2) limbs), r = v % p ((n,) for b <= 64, (n,2) for b = 89);
+    v is an (n, 2) int64/uint64 tensor of (lo, hi) limbs."""
+    n = v.numel() // 2
+    if want_q and q is None:
+        q = torch.empty((n, 2), dtype=torch.int64, device=v.device)
+    if want_r and r is None:
+        r = torch.empty((n, 2) if b > 64 else (n,), dtype=torch.int64, device=v.device)
+    _check(_load().ms_div(b, c, _ptr(v), _ptr(q) if want_q else None,
+                          _ptr(r) if want_r else None, n, _stream(stream)), "ms_div")
+    return q, r
+
+
+def mod(b: int, c: int, v: torch.Tensor, r: torch.Tensor | None = None, stream=None):
+    n = v.numel() // 2
+    if r is None:
+        r = torch.empty((n, 2) if b > 64 else (n,), dtype=torch.int64, device=v.device)
+    _check(_load().ms_mod(b, c, _ptr(v), _ptr(r), n, _stream(stream)), "ms_mod")
+    return r
+
+
+# ------------------------------------------------------------------ sketch
+
+class _CudaView:
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+        self._owner = owner
+
+
+class Sketch:
+    """A t-row Count Sketch with m counters per row (cs_*)."""
+
+    def __init__(self, t: int = 5, m: int = 1024, k: int = 4, b: int = 61, c: int = 1,
+                 seed: int = 0, mode: int = TWO_FOR_ONE, coeffs=None, _handle=None):
+        lib_ = _load()
+        if _handle is not None:
+            h = _handle
+        else:
+            h = ctypes.c_void_p()
+            if coeffs is None:
+                _check(lib_.cs_create(ctypes.byref(h), t, m, k, b, c, seed, mode), "cs_create")
+            else:
+                arr = _u128_array(coeffs)
+                _check(lib_.cs_create_coeffs(ctypes.byref(h), t, m, k, b, c, mode, arr),
+                       "cs_create_coeffs")
+        self._h = h
+        tt, mm, kk, bb, md = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_int(), ctypes.c_int(), \
+            ctypes.c_int()
+        cc = ctypes.c_uint64()
+        _check(lib_.cs_params(h, ctypes.byref(tt), ctypes.byref(mm), ctypes.byref(kk),
+                              ctypes.byref(bb), ctypes.byref(cc), ctypes.byref(md)), "cs_params")
+        self.t, self.m, self.k, self.b, self.c, self.mode = (tt.value, mm.value, kk.value,
+                                                             bb.value, cc.value, md.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def coeffs(self) -> list:
+        n = self.t * self.k * (2 if self.mode == TWO_POLY else 1)
+        arr = (U128 * n)()
+        _check(_load().cs_coeffs(self._h, arr), "cs_coeffs")
+        return [a.lo | (a.hi << 64) for a in arr]
+
+    def update(self, keys: torch.Tensor, weights: torch.Tensor | None = None, stream=None):
+        n = _nkeys(keys, self.b, self.c)
+        if weights is not None and weights.numel() != n:
+            raise ValueError("weights must have one entry per key")
+        if weights is not None and weights.dtype != torch.int32:
+            raise TypeError("weights must be int32")
+        _check(_load().cs_update(self._h, _ptr(keys), _ptr(weights), n, _stream(stream)),
+               "cs_update")
+
+    def estimate_f2(self, out: torch.Tensor | None = None, rows: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+        """Device tensor (2,) int64 holding the 128-bit estimate as (lo, hi)."""
+        if out is None:
+            out = torch.empty(2, dtype=torch.int64, device="cuda")
+        _check(_load().cs_estimate_f2(self._h, _ptr(out), _ptr(rows), _stream(stream)),
+               "cs_estimate_f2")
+        return out
+
+    def f2(self) -> int:
+        """The F2 estimate as a Python int (synchronizes)."""
+        o = self.estimate_f2().cpu()
+        return u128_to_int(o)
+
+    def row_values(self) -> list:
+        rows = torch.empty((self.t, 2), dtype=torch.int64, device="cuda")
+        self.estimate_f2(rows=rows)
+        return [u128_to_int(r) for r in rows.cpu()]
+
+    def point_query(self, keys: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        n = _nkeys(keys, self.b, self.c)
+        if out is None:
+            out = torch.empty(n, dtype=torch.int64, device=keys.device)
+        _check(_load().cs_point_query(self._h, _ptr(keys), _ptr(out), n, _stream(stream)),
+               "cs_point_query")
+        return out
+
+    def counters(self) -> torch.Tensor:
+        """Zero-copy (t, m) int64 view of the library-owned counters."""
+        p = ctypes.c_void_p()
+        _check(_load().cs_counters(self._h, ctypes.byref(p)), "cs_counters")
+        return torch.as_tensor(_CudaView(p.value, (self.t, self.m), "<i8", self), device="cuda")
+
+    def reset(self, stream=None):
+        _check(_load().cs_reset(self._h, _stream(stream)), "cs_reset")
+
+    def merge(self, other: "Sketch", stream=None):
+        _check(_load().cs_merge(self._h, other._h, _stream(stream)), "cs_merge")
+
+    def export(self, stream=None) -> bytes:
+        size = ctypes.c_size_t(0)
+        _check(_load().cs_export(self._h, None, ctypes.byref(size), _stream(stream)), "cs_export")
+        buf = ctypes.create_string_buffer(size.value)
+        _check(_load().cs_export(self._h, buf, ctypes.byref(size), _stream(stream)), "cs_export")
+        return buf.raw[:size.value]
+
+    @classmethod
+    def import_(cls, data: bytes) -> "Sketch":
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(_load().cs_import(ctypes.byref(h), buf, len(data)), "cs_import")
+        return cls(_handle=h)
+
+    def set_launch(self, place: int = -1, strategy: int = -1, threads: int = 0, blocks: int = 0,
+                   blocks_per_sm: int = 0, cluster: int = 0):
+        _check(_load().cs_set_launch(self._h, place, strategy, threads, blocks, blocks_per_sm,
+                                     cluster), "cs_set_launch")
+
+    def last_launch(self) -> dict:
+        v = [ctypes.c_int() for _ in range(7)]
+        _check(_load().cs_last_launch(self._h, *[ctypes.byref(x) for x in v]), "cs_last_launch")
+        keys = ("place", "strategy", "threads", "blocks", "cluster", "smem", "specialized")
+        return dict(zip(keys, [x.value for x in v]))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.cs_destroy(self._h)
+            self._h = None
+
+
+# ------------------------------------------------------------------ helpers
+
+def u128_to_int(t) -> int:
+    lo, hi = int(t[0]), int(t[1])
+    return (lo & ((1 << 64) - 1)) | ((hi & ((1 << 64) - 1)) << 64)
+
+
+def probe_mul128(variant: int = 0, iters: int = 4096) -> tuple:
+    """(products per second, kernel ms) of the integer-multiply probe."""
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_load().ms_probe_mul128(variant, iters, _ptr(sink), ctypes.byref(rate),
+                                   ctypes.byref(ms)), "ms_probe_mul128")
+    return rate.value, ms.value

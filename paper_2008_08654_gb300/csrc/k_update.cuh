@@ -1,0 +1,413 @@
+// Count Sketch update kernel (Algorithm count-sketch "Process", Sec. 1.4) and
+// the per-prime hashing glue it needs.  Included by one translation unit per
+// prime, which instantiates the launch dispatcher for that prime.
+//
+// Per block:
+//   1. zero its counter tile (PLACE_SMEM: all t x m counters as int32 in shared
+//      memory; PLACE_DSMEM: a 1/cluster slice of every row, the slices of the
+//      cluster's blocks together covering the sketch; PLACE_GLOBAL: none);
+//   2. grid-stride over groups of 4 consecutive keys (16-byte vector loads when
+//      aligned), reduce each key mod p, hash it with every row's polynomial,
+//      split each hash value into (bucket, sign) (Algorithm h-and-s), and add
+//      sign * weight to the counter with a shared-memory (or distributed
+//      shared-memory) atomic;
+//   3. add its tile into the int64 counters in global memory (a sketch is
+//      linear in the stream, so per-block partial sketches add up exactly).
+// Weights whose magnitude could overflow an int32 tile counter (|w| > w_safe,
+// computed on the host from the keys one tile can see) go straight to the
+// int64 counters instead, so the result is exact for every int32 weight.
+#pragma once
+
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "ms_field.cuh"
+#include "ms_kernels.h"
+
+namespace msk {
+
+using msf::u128;
+using msf::u128x;
+
+// ------------------------------------------------------------ field glue
+//
+// FieldOps<F> gives a uniform interface over the four primes:
+//   val_t         hash value type used in registers
+//   Prep          a key prepared for multiplication (reduced, maybe split)
+//   prep(key)     key -> Prep
+//   mul_add(z, P, a)  lazy  z*x + a
+//   canon(y)      final canonical residue
+//   from_words(w) coefficient from its 64-bit limbs
+template <class F>
+struct FieldOps;
+
+template <>
+struct FieldOps<msf::P61> {
+    typedef msf::P61 F;
+    typedef u64 val_t;
+    typedef F::Split Prep;
+    typedef u64 key_t;
+    static constexpr int WORDS = 1;
+    __device__ static __forceinline__ Prep prep(u64 key) { return F::split(F::reduce_key(key)); }
+    __device__ static __forceinline__ val_t mul_add(val_t z, const Prep& x, val_t a) {
+        return F::mul_add(z, x, a);
+    }
+    __device__ static __forceinline__ val_t canon(val_t y) { return F::canon(y); }
+    __device__ static __forceinline__ val_t from_words(const u64* w) { return w[0]; }
+    __device__ static __forceinline__ u32 bucket(val_t h, u32 mask) { return F::bucket(h, mask); }
+    __device__ static __forceinline__ u32 sign_bit(val_t h) { return F::sign_bit(h); }
+};
+
+template <>
+struct FieldOps<msf::P31> {
+    typedef msf::P31 F;
+    typedef u32 val_t;
+    typedef u32 Prep;
+    typedef u32 key_t;
+    static constexpr int WORDS = 1;
+    __device__ static __forceinline__ Prep prep(u32 key) { return F::reduce_key(key); }
+    __device__ static __forceinline__ val_t mul_add(val_t z, const Prep& x, val_t a) {
+        return F::mul_add(z, x, a);
+    }
+    __device__ static __forceinline__ val_t canon(val_t y) { return F::canon(y); }
+    __device__ static __forceinline__ val_t from_words(const u64* w) { return (u32)w[0]; }
+    __device__ static __forceinline__ u32 bucket(val_t h, u32 mask) { return F::bucket(h, mask); }
+    __device__ static __forceinline__ u32 sign_bit(val_t h) { return F::sign_bit(h); }
+};
+
+template <>
+struct FieldOps<msf::P64> {
+    typedef msf::P64 F;
+    typedef u64 val_t;
+    typedef u64 Prep;
+    typedef u64 key_t;
+    static constexpr int WORDS = 1;
+    __device__ static __forceinline__ Prep prep(u64 key) { return F::reduce_key(key); }
+    __device__ static __forceinline__ val_t mul_add(val_t z, const Prep& x, val_t a) {
+        return F::mul_add(z, x, a);
+    }
+    __device__ static __forceinline__ val_t canon(val_t y) { return y; }  // already canonical
+    __device__ static __forceinline__ val_t from_words(const u64* w) { return w[0]; }
+    __device__ static __forceinline__ u32 bucket(val_t h, u32 mask) { return F::bucket(h, mask); }
+    __device__ static __forceinline__ u32 sign_bit(val_t h) { return F::sign_bit(h); }
+};
+
+template <>
+struct FieldOps<msf::P89> {
+    typedef msf::P89 F;
+    typedef u128 val_t;
+    typedef u128 Prep;
+    typedef u128x key_t;
+    static constexpr int WORDS = 2;
+    __device__ static __forceinline__ Prep prep(const u128x& key) {
+        return F::reduce_key(F::load(key));
+    }
+    __device__ static __forceinline__ val_t mul_add(val_t z, const Prep& x, val_t a) {
+        return F::mul_add(z, x, a);
+    }
+    __device__ static __forceinline__ val_t canon(val_t y) { return F::canon(y); }
+    __device__ static __forceinline__ val_t from_words(const u64* w) {
+        return ((u128)w[1] << 64) | w[0];
+    }
+    __device__ static __forceinline__ u32 bucket(val_t h, u32 mask) { return F::bucket(h, mask); }
+    __device__ static __forceinline__ u32 sign_bit(val_t h) { return F::sign_bit(h); }
+};
+
+// ------------------------------------------------------------ coefficients
+//
+// Compile-time (t, k): the coefficients travel in the kernel's parameter
+// space.  With the row and coefficient loops unrolled, every access has a
+// constant offset, so the multiply instructions read them straight from the
+// constant bank.  For p = 2^61-1 the 31-bit splits used by the power-sum
+// evaluation are precomputed on the host.
+template <class F, int NFUN, int K>
+struct ParamCoef {
+    u64 w[NFUN > 0 ? NFUN * K * FieldOps<F>::WORDS : 1];
+    u32 lo[NFUN > 0 ? NFUN * K : 1];  // P61 only: a & (2^31-1)
+    u32 hi[NFUN > 0 ? NFUN * K : 1];  // P61 only: a >> 31
+};
+
+// Coefficient a_i of function f.  Generic kernels read the shared-memory copy
+// (k runtime); specialized kernels index the parameter struct directly, so
+// after unrolling each access is a constant-bank operand.
+template <class F, int NFUN, int K>
+__device__ __forceinline__ typename FieldOps<F>::val_t coef_at(const ParamCoef<F, NFUN, K>& pc,
+                                                               const u64* scoef, bool generic,
+                                                               int k, int f, int i) {
+    typedef typename FieldOps<F>::val_t val_t;
+    constexpr int W = FieldOps<F>::WORDS;
+    if (generic) {
+        const u64* w = scoef + ((size_t)f * k + i) * W;
+        if (W == 1) return (val_t)w[0];
+        return (val_t)(((u128)w[1] << 64) | w[0]);
+    }
+    const int idx = f * K + i;
+    if (W == 1) return (val_t)pc.w[idx];
+    return (val_t)(((u128)pc.w[2 * idx + 1] << 64) | pc.w[2 * idx]);
+}
+
+// ------------------------------------------------------------ key loading
+//
+// load4: 4 consecutive keys and weights starting at index j (j % 4 == 0).
+// Returns how many are in range; out-of-range keys read as 0 with weight 0.
+template <class F>
+struct KeyIO;
+
+template <>
+struct KeyIO<msf::P61> {
+    __device__ static __forceinline__ void load(const void* keys, u64 j, u64 n, bool vec,
+                                                u64 (&x)[4]) {
+        const u64* k = (const u64*)keys + j;
+        if (vec && j + 3 < n) {
+            const ulonglong2 a = __ldcs((const ulonglong2*)k);
+            const ulonglong2 b = __ldcs((const ulonglong2*)k + 1);
+            x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = (j + q < n) ? __ldcs(k + q) : 0ull;
+        }
+    }
+};
+template <>
+struct KeyIO<msf::P64> : KeyIO<msf::P61> {};
+
+template <>
+struct KeyIO<msf::P31> {
+    __device__ static __forceinline__ void load(const void* keys, u64 j, u64 n, bool vec,
+                                                u32 (&x)[4]) {
+        const u32* k = (const u32*)keys + j;
+        if (vec && j + 3 < n) {
+            const uint4 a = __ldcs((const uint4*)k);
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = (j + q < n) ? __ldcs(k + q) : 0u;
+        }
+    }
+};
+
+template <>
+struct KeyIO<msf::P89> {
+    __device__ static __forceinline__ void load(const void* keys, u64 j, u64 n, bool vec,
+                                                u128x (&x)[4]) {
+        const ulonglong2* k = (const ulonglong2*)keys + j;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ulonglong2 v = make_ulonglong2(0ull, 0ull);
+            if (j + q < n) v = __ldcs(k + q);  // 16-byte keys: always one vector load
+            x[q].lo = v.x;
+            x[q].hi = v.y;
+        }
+        (void)vec;
+    }
+};
+
+__device__ __forceinline__ void load_weights4(const int32_t* w, u64 j, u64 n, bool vec,
+                                              int (&wt)[4]) {
+    if (w == nullptr) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wt[q] = (j + q < n) ? 1 : 0;
+        return;
+    }
+    if (vec && j + 3 < n) {
+        const int4 a = __ldcs((const int4*)(w + j));
+        wt[0] = a.x; wt[1] = a.y; wt[2] = a.z; wt[3] = a.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wt[q] = (j + q < n) ? __ldcs(w + q + j) : 0;
+    }
+}
+
+// ------------------------------------------------------------ cluster helpers
+
+__device__ __forceinline__ u32 cluster_rank() {
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Adds v to the 32-bit counter at shared address `laddr` of block `rank` of
+// this cluster.
+__device__ __forceinline__ void dsmem_add(u32 laddr, u32 rank, int v) {
+    u32 raddr;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(rank));
+    asm volatile("red.relaxed.cluster.shared::cluster.add.u32 [%0], %1;" ::"r"(raddr), "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ void global_add64(long long* p, long long v) {
+    atomicAdd((unsigned long long*)p, (unsigned long long)v);
+}
+
+// ------------------------------------------------------------ the kernel
+
+// One counter update: C[row][bucket] += (sign ? -w : w).
+template <int PLACE>
+__device__ __forceinline__ void apply_update(int* tile, u32 tile_saddr, long long* counters,
+                                             int row, u32 bucket, u32 sign, int w, bool big,
+                                             u32 m, int log2m, int lcs) {
+    if (PLACE == PLACE_GLOBAL || big) {
+        const long long d = sign ? -(long long)w : (long long)w;
+        global_add64(counters + (((u64)row) << log2m) + bucket, d);
+        return;
+    }
+    const int d = sign ? -w : w;
+    if (PLACE == PLACE_SMEM) {
+        atomicAdd(tile + (row << log2m) + bucket, d);
+    } else {  // PLACE_DSMEM: owner block = high bits of the bucket
+        const int lshift = log2m - lcs;
+        const u32 owner = bucket >> lshift;
+        const u32 local = ((u32)row << lshift) + (bucket & ((1u << lshift) - 1u));
+        dsmem_add(tile_saddr + local * 4u, owner, d);
+    }
+}
+
+// T, K > 0: compile-time rows and degree with ParamCoef; T = K = 0: runtime t
+// and k with coefficients staged from coef_dev into shared memory.
+template <class F, int T, int K, int MODE, int PLACE, int STRAT>
+__global__ void __launch_bounds__(512)
+k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1) * T, K> pc) {
+    typedef FieldOps<F> Ops;
+    typedef typename Ops::val_t val_t;
+    typedef typename Ops::Prep Prep;
+    constexpr int NF = (MODE == CS_TWO_POLY) ? 2 : 1;
+    constexpr bool GENERIC = (T == 0);
+    constexpr int W = Ops::WORDS;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int t = GENERIC ? a.t : T;
+    const int k = GENERIC ? a.k : K;
+    const int log2m = a.log2m;
+    const u32 m = 1u << log2m;
+    const u32 mask = m - 1u;
+    const int lcs = (PLACE == PLACE_DSMEM) ? a.cluster_log2 : 0;
+    const u32 mloc = m >> lcs;
+
+    int* tile = reinterpret_cast<int*>(smem);
+    const u32 tile_cells = (PLACE == PLACE_GLOBAL) ? 0u : (u32)t * mloc;
+    u64* scoef = reinterpret_cast<u64*>(smem + (size_t)tile_cells * 4u);
+    const u32 tile_saddr = (u32)__cvta_generic_to_shared(tile);
+
+    for (u32 i = threadIdx.x; i < tile_cells; i += blockDim.x) tile[i] = 0;
+    if (GENERIC) {
+        const int nw = t * NF * k * W;
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) scoef[i] = a.coef_dev[i];
+    }
+    __syncthreads();
+    if (PLACE == PLACE_DSMEM) cluster_sync_all();
+
+    // coefficient a_i of function f (row r: bucket f = r*NF, sign f = r*NF+1)
+#define MSK_COEF(f, i) coef_at<F, NF * T, K>(pc, scoef, GENERIC, k, (f), (i))
+
+    const u64 n = a.n;
+    const bool vec = a.vec_ok != 0;
+    const u32 w_safe = a.w_safe;
+    const u64 stride = (u64)gridDim.x * blockDim.x * 4ull;
+    for (u64 j = ((u64)blockIdx.x * blockDim.x + threadIdx.x) * 4ull; j < n; j += stride) {
+        typename Ops::key_t key[4];
+        int wt[4];
+        KeyIO<F>::load(a.keys, j, n, vec, key);
+        load_weights4(a.weights, j, n, vec, wt);
+        bool big[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const u32 aw = wt[q] < 0 ? 0u - (u32)wt[q] : (u32)wt[q];
+            big[q] = aw > w_safe;
+        }
+
+        if constexpr (!GENERIC && STRAT == STRAT_POWER_SUM && std::is_same<F, msf::P61>::value &&
+                      K == 4) {
+            // x, x^2, x^3 once per key, shared by every row's polynomial(s).
+            typename msf::P61::Split xp[4][3];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const u64 x1 = msf::P61::reduce_key(key[q]);
+                xp[q][0] = msf::P61::split(x1);
+                const u64 x2 = msf::P61::mul_add(x1, xp[q][0], 0ull);
+                xp[q][1] = msf::P61::split(x2);
+                const u64 x3 = msf::P61::mul_add(x2, xp[q][0], 0ull);
+                xp[q][2] = msf::P61::split(x3);
+            }
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                const int fb = r * NF;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const u32 al[3] = {pc.lo[fb * 4 + 1], pc.lo[fb * 4 + 2], pc.lo[fb * 4 + 3]};
+                    const u32 ah[3] = {pc.hi[fb * 4 + 1], pc.hi[fb * 4 + 2], pc.hi[fb * 4 + 3]};
+                    const u64 h = msf::P61::power_sum<3>(xp[q], pc.w[fb * 4], al, ah);
+                    u32 sb;
+                    if (MODE == CS_TWO_POLY) {
+                        const int fs = fb + 1;
+                        const u32 sl[3] = {pc.lo[fs * 4 + 1], pc.lo[fs * 4 + 2], pc.lo[fs * 4 + 3]};
+                        const u32 sh[3] = {pc.hi[fs * 4 + 1], pc.hi[fs * 4 + 2], pc.hi[fs * 4 + 3]};
+                        const u64 g = msf::P61::power_sum<3>(xp[q], pc.w[fs * 4], sl, sh);
+                        sb = msf::P61::sign_bit(g);
+                    } else {
+                        sb = msf::P61::sign_bit(h);
+                    }
+                    if (wt[q] != 0)
+                        apply_update<PLACE>(tile, tile_saddr, a.counters, r,
+                                            msf::P61::bucket(h, mask), sb, wt[q], big[q], m, log2m,
+                                            lcs);
+                }
+            }
+        } else {
+            Prep xp[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xp[q] = Ops::prep(key[q]);
+#pragma unroll(GENERIC ? 1 : (T > 0 ? T : 1))
+            for (int r = 0; r < t; ++r) {
+                const int fb = r * NF;
+                val_t h[4], g[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    val_t y = MSK_COEF(fb, k - 1);
+#pragma unroll(GENERIC ? 1 : (K > 1 ? K - 1 : 1))
+                    for (int i = k - 2; i >= 0; --i) y = Ops::mul_add(y, xp[q], MSK_COEF(fb, i));
+                    h[q] = Ops::canon(y);
+                    if (MODE == CS_TWO_POLY) {
+                        val_t z = MSK_COEF(fb + 1, k - 1);
+#pragma unroll(GENERIC ? 1 : (K > 1 ? K - 1 : 1))
+                        for (int i = k - 2; i >= 0; --i) z = Ops::mul_add(z, xp[q], MSK_COEF(fb + 1, i));
+                        g[q] = Ops::canon(z);
+                    } else {
+                        g[q] = h[q];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (wt[q] != 0)
+                        apply_update<PLACE>(tile, tile_saddr, a.counters, r, Ops::bucket(h[q], mask),
+                                            Ops::sign_bit(g[q]), wt[q], big[q], m, log2m, lcs);
+                }
+            }
+        }
+    }
+
+#undef MSK_COEF
+
+    if (PLACE == PLACE_GLOBAL) return;
+    if (PLACE == PLACE_DSMEM)
+        cluster_sync_all();  // every remote add into this block's slice has landed
+    else
+        __syncthreads();
+    const u32 rank = (PLACE == PLACE_DSMEM) ? cluster_rank() : 0u;
+    const int lshift = log2m - lcs;
+    for (u32 i = threadIdx.x; i < tile_cells; i += blockDim.x) {
+        const int v = tile[i];
+        if (v != 0) {
+            const u32 row = i >> lshift;
+            const u32 b = (rank << lshift) + (i & (mloc - 1u));
+            global_add64(a.counters + (((u64)row) << log2m) + b, (long long)v);
+        }
+    }
+}
+
+}  // namespace msk

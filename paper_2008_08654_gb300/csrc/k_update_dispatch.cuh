@@ -1,0 +1,119 @@
+// Runtime -> compile-time dispatch of the Count Sketch update kernel for one
+// prime.  Each k_update_p*.cu includes this file and instantiates
+// launch_update_for<F>() for its prime, so the four primes compile in
+// parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "k_update.cuh"
+
+namespace msk {
+
+// Fill the parameter-space coefficient pack from the host copy of the
+// coefficient words (function-major, a_0 first, W limbs each).
+template <class F, int NFUN, int K>
+static void fill_param_coef(ParamCoef<F, NFUN, K>& pc, const u64* words) {
+    constexpr int W = FieldOps<F>::WORDS;
+    if (NFUN == 0) {
+        pc.w[0] = 0;
+        pc.lo[0] = pc.hi[0] = 0;
+        return;
+    }
+    for (int i = 0; i < NFUN * K * W; ++i) pc.w[i] = words[i];
+    for (int i = 0; i < NFUN * K; ++i) {
+        const u64 a = words[i * W];
+        pc.lo[i] = (u32)(a & 0x7FFFFFFFull);
+        pc.hi[i] = (u32)(a >> 31);
+    }
+}
+
+template <class F, int T, int K, int MODE, int PLACE, int STRAT>
+static cudaError_t launch_exact(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                                cudaStream_t stream, int* occupancy) {
+    constexpr int NF = (MODE == CS_TWO_POLY) ? 2 : 1;
+    auto kern = k_cs_update<F, T, K, MODE, PLACE, STRAT>;
+    cudaError_t e;
+    if (cfg.smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (PLACE == PLACE_DSMEM && cfg.cluster > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)cfg.blocks);
+    lc.blockDim = dim3((unsigned)cfg.threads);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    if (PLACE == PLACE_DSMEM) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cfg.cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+    }
+    if (occupancy) {
+        if (PLACE == PLACE_DSMEM)
+            return cudaOccupancyMaxActiveClusters(occupancy, kern, &lc);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, kern, cfg.threads,
+                                                             cfg.smem);
+    }
+    ParamCoef<F, NF * T, K> pc;
+    fill_param_coef<F, NF * T, K>(pc, coef_host);
+    return cudaLaunchKernelEx(&lc, kern, a, pc);
+}
+
+template <class F, int T, int K, int MODE>
+static cudaError_t launch_place(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                                cudaStream_t stream, int* occupancy) {
+    constexpr bool PS_OK = std::is_same<F, msf::P61>::value && K == 4;
+    const bool ps = PS_OK && cfg.strategy == STRAT_POWER_SUM;
+    switch (cfg.place) {
+        case PLACE_SMEM:
+            return ps ? launch_exact<F, T, K, MODE, PLACE_SMEM, PS_OK ? STRAT_POWER_SUM : STRAT_HORNER>(
+                            a, coef_host, cfg, stream, occupancy)
+                      : launch_exact<F, T, K, MODE, PLACE_SMEM, STRAT_HORNER>(a, coef_host, cfg,
+                                                                              stream, occupancy);
+        case PLACE_DSMEM:
+            return ps ? launch_exact<F, T, K, MODE, PLACE_DSMEM, PS_OK ? STRAT_POWER_SUM : STRAT_HORNER>(
+                            a, coef_host, cfg, stream, occupancy)
+                      : launch_exact<F, T, K, MODE, PLACE_DSMEM, STRAT_HORNER>(a, coef_host, cfg,
+                                                                               stream, occupancy);
+        default:
+            return ps ? launch_exact<F, T, K, MODE, PLACE_GLOBAL, PS_OK ? STRAT_POWER_SUM : STRAT_HORNER>(
+                            a, coef_host, cfg, stream, occupancy)
+                      : launch_exact<F, T, K, MODE, PLACE_GLOBAL, STRAT_HORNER>(a, coef_host, cfg,
+                                                                                stream, occupancy);
+    }
+}
+
+template <class F, int T, int K>
+static cudaError_t launch_mode(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                               cudaStream_t stream, int* occupancy) {
+    if (a.mode == CS_TWO_POLY)
+        return launch_place<F, T, K, CS_TWO_POLY>(a, coef_host, cfg, stream, occupancy);
+    return launch_place<F, T, K, CS_TWO_FOR_ONE>(a, coef_host, cfg, stream, occupancy);
+}
+
+// The specializations: (t, k) = (5, 4) and (7, 4), the workloads' shapes;
+// everything else takes the generic kernel (runtime t and k).
+template <class F>
+cudaError_t launch_update_for(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                              cudaStream_t stream, int* specialized, int* occupancy) {
+    if (a.k == 4 && a.t == 5) {
+        if (specialized) *specialized = 1;
+        return launch_mode<F, 5, 4>(a, coef_host, cfg, stream, occupancy);
+    }
+    if (a.k == 4 && a.t == 7) {
+        if (specialized) *specialized = 1;
+        return launch_mode<F, 7, 4>(a, coef_host, cfg, stream, occupancy);
+    }
+    if (specialized) *specialized = 0;
+    return launch_mode<F, 0, 0>(a, coef_host, cfg, stream, occupancy);
+}
+
+}  // namespace msk

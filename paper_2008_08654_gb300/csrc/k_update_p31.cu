@@ -1,0 +1,12 @@
+// Count Sketch update kernels for the prime msf::P31 (one translation unit per
+// prime so that they compile in parallel).
+#include "k_update_dispatch.cuh"
+
+namespace msk {
+
+cudaError_t launch_update_p31(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                              cudaStream_t stream, int* specialized, int* occupancy) {
+    return launch_update_for<msf::P31>(a, coef_host, cfg, stream, specialized, occupancy);
+}
+
+}  // namespace msk

@@ -1,0 +1,228 @@
+// Device arithmetic modulo p = 2^b - c for the four supported primes.
+//
+// Each policy struct gives, for its prime:
+//   key_t / val_t     key and hash-value types,
+//   reduce_key(x)     x mod p, canonical,
+//   Horner / power-sum building blocks with LAZY reduction: intermediate
+//                     values stay below 2^b + 2^4 (not necessarily < p), and
+//                     only the final value is made canonical,
+//   bucket(h, mask)   the low bits of h (Algorithm h-and-s, Sec. 1.4),
+//   sign_bit(h)       bit b-1 of h (the same algorithm).
+//
+// Mersenne reduction uses the fold y = (y mod 2^b) + floor(y / 2^b), which
+// preserves y mod p because 2^b = 1 (mod p) (eq. Mersenne, Sec. 1.2).  The
+// pseudo-Mersenne prime 2^64 - 59 uses Algorithm division-generalized and
+// Algorithm mod-generalized (Sec. 1.6) with 3 steps.
+//
+// Every bound below is for the stated input ranges; the comments give the
+// arithmetic so that each can be checked by hand.
+#pragma once
+
+#include <stdint.h>
+
+namespace msf {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+typedef unsigned __int128 u128;
+
+struct u128x {  // a two-limb key/value as it sits in memory
+    u64 lo, hi;
+};
+
+// ---------------------------------------------------------------- p = 2^61-1
+//
+// Elements are split into a 31-bit low part and a high part,
+//     z = zh * 2^31 + zl,  zl < 2^31,
+// so that every partial product fits 62 bits and sums of a few of them never
+// carry out of 64 bits.  For z < 2^61 + 2^4 we have zh <= 2^30.
+struct P61 {
+    static constexpr int B = 61;
+    static constexpr u64 P = (1ull << 61) - 1;
+    typedef u64 key_t;
+    typedef u64 val_t;
+
+    struct Split {  // of a value < 2^61 + 2^4
+        u32 lo;     // < 2^31
+        u32 hi;     // <= 2^30
+        u32 hi2;    // 2 * hi <= 2^31
+    };
+
+    __device__ static __forceinline__ Split split(u64 z) {
+        Split s;
+        s.lo = (u32)z & 0x7FFFFFFFu;
+        s.hi = (u32)(z >> 31);
+        s.hi2 = s.hi << 1;
+        return s;
+    }
+
+    // x mod p for any 64-bit x: (x & p) + (x >> 61) < 2^61 + 8 < 2p.
+    __device__ static __forceinline__ u64 reduce_key(u64 x) {
+        return canon((x & P) + (x >> 61));
+    }
+
+    // y < 2p  ->  y mod p
+    __device__ static __forceinline__ u64 canon(u64 y) { return y >= P ? y - P : y; }
+
+    // Fold of a 64-bit value: (S & p) + (S >> 61) = S (mod p), result < 2^61 + 8.
+    __device__ static __forceinline__ u64 fold(u64 S) { return (S & P) + (S >> 61); }
+
+    // One Horner step (Algorithm Mersenne): returns y = z*x + a (mod p), lazily
+    // reduced (< 2^61 + 8), for z < 2^61 + 8, x canonical (xs = split(x)),
+    // a < 2^61.
+    //   z*x = zh*xh*2^62 + (zh*xl + zl*xh)*2^31 + zl*xl,   2^62 = 2 (mod p)
+    //   A = zl*xl + a + zh*(2xh)   <= (2^31-1)^2 + 2^61 + 2^30*(2^31-2) < 2^63
+    //   M = zh*xl + zl*xh          <  2^30*2^31 + 2^31*2^30 = 2^62
+    //   M*2^31 = (M >> 30)*2^61 + (M mod 2^30)*2^31 = (M >> 30) + (M mod 2^30)*2^31
+    //   S = A + (M >> 30) + (M mod 2^30)*2^31  < 2^63 + 2^32 + 2^61 < 2^64
+    __device__ static __forceinline__ u64 mul_add(u64 z, const Split& xs, u64 a) {
+        const u32 zl = (u32)z & 0x7FFFFFFFu;
+        const u32 zh = (u32)(z >> 31);
+        u64 A = (u64)zl * xs.lo + a;
+        A += (u64)zh * xs.hi2;
+        u64 M = (u64)zh * xs.lo;
+        M += (u64)zl * xs.hi;
+        const u64 S = A + (M >> 30) + ((M & 0x3FFFFFFFull) << 31);
+        return fold(S);
+    }
+
+    // Power-sum row hash for k = 4 (Sec. 1.2 definition h = sum a_i x^i):
+    // given splits of x, x^2, x^3 (lazy, < 2^61 + 8) and the row's coefficients
+    // a_0 (full) and split a_1..a_3 (al < 2^31, ah < 2^30):
+    //   A = a_0 + sum al_i*xl_i              < 2^61 + 3*2^62           < 2^64
+    //   H = sum ah_i*(2 xh_i)                <= 3 * 2^30 * 2^31       = 3*2^61
+    //   M = sum (ah_i*xl_i + al_i*xh_i)      < 6 * 2^61               < 2^64
+    //   S = fold(A) + H + (M >> 30) + (M mod 2^30)*2^31
+    //                                         < 2^61+8 + 3*2^61 + 2^34 + 2^61 < 2^64
+    // Returns the canonical hash value.
+    template <int KM1>
+    __device__ static __forceinline__ u64 power_sum(const Split* xp, u64 a0, const u32* al,
+                                                    const u32* ah) {
+        static_assert(KM1 >= 1 && KM1 <= 3, "at most 3 lazy terms per accumulator");
+        u64 A = a0, H = 0, M = 0;
+#pragma unroll
+        for (int i = 0; i < KM1; ++i) {
+            A += (u64)al[i] * xp[i].lo;
+            H += (u64)ah[i] * xp[i].hi2;
+            M += (u64)ah[i] * xp[i].lo;
+            M += (u64)al[i] * xp[i].hi;
+        }
+        const u64 S = fold(A) + H + (M >> 30) + ((M & 0x3FFFFFFFull) << 31);
+        return canon(fold(S));
+    }
+
+    __device__ static __forceinline__ u32 bucket(u64 h, u32 mask) { return (u32)h & mask; }
+    __device__ static __forceinline__ u32 sign_bit(u64 h) { return (u32)(h >> 60) & 1u; }
+};
+
+// ---------------------------------------------------------------- p = 2^31-1
+struct P31 {
+    static constexpr int B = 31;
+    static constexpr u32 P = 0x7FFFFFFFu;
+    typedef u32 key_t;
+    typedef u32 val_t;
+
+    // x < 2^32: (x & p) + (x >> 31) <= 2^31 - 1 + 1 = 2^31 < 2p.
+    __device__ static __forceinline__ u32 reduce_key(u32 x) { return canon((x & P) + (x >> 31)); }
+    __device__ static __forceinline__ u32 canon(u32 y) { return y >= P ? y - P : y; }
+
+    // y = z*x + a (mod p), lazily reduced (< 2^31 + 3), for z < 2^31 + 3,
+    // x < p, a < p:
+    //   v = z*x + a < (2^31+3)*2^31 + 2^31 < 2^63
+    //   f = (v & p) + (v >> 31) < 2^31 + 2^32 + 4
+    //   (f & p) + (f >> 31) < 2^31 + 3
+    __device__ static __forceinline__ u32 mul_add(u32 z, u32 x, u32 a) {
+        u64 v = (u64)z * x + a;
+        v = (v & P) + (v >> 31);
+        return (u32)((v & P) + (v >> 31));
+    }
+
+    __device__ static __forceinline__ u32 bucket(u32 h, u32 mask) { return h & mask; }
+    __device__ static __forceinline__ u32 sign_bit(u32 h) { return (h >> 30) & 1u; }
+};
+
+// ---------------------------------------------------------------- p = 2^89-1
+//
+// Values are unsigned __int128 below 2^89 + 2^4 (lazy).
+struct P89 {
+    static constexpr int B = 89;
+    typedef u128x key_t;
+    typedef u128x val_t;
+
+    __device__ static __forceinline__ u128 Pv() { return (((u128)1) << 89) - 1; }
+
+    __device__ static __forceinline__ u128 load(const u128x& v) {
+        return ((u128)v.hi << 64) | v.lo;
+    }
+    __device__ static __forceinline__ u128x store(u128 v) {
+        u128x r;
+        r.lo = (u64)v;
+        r.hi = (u64)(v >> 64);
+        return r;
+    }
+
+    // x < 2^128: (x & p) + (x >> 89) < 2^89 + 2^39 < 2p.
+    __device__ static __forceinline__ u128 reduce_key(u128 x) {
+        return canon((x & Pv()) + (x >> 89));
+    }
+    __device__ static __forceinline__ u128 canon(u128 y) { return y >= Pv() ? y - Pv() : y; }
+
+    // y = z*x + a (mod p), lazily reduced (< 2^89 + 4), for z < 2^89 + 4,
+    // x < p, a < p.  With z = z1*2^64 + z0, x = x1*2^64 + x0 (z1 <= 2^25,
+    // x1 < 2^25):
+    //   z*x = z1 x1 2^128 + (z1 x0 + z0 x1) 2^64 + z0 x0
+    //   2^128 = 2^39 (mod p), so z1 x1 2^128 = z1 x1 2^39, and z1 x1 2^39 < 2^89+2^64
+    //   T = z1 x0 + z0 x1 < 2^90;  T 2^64 = (T >> 25) + (T mod 2^25) 2^64  (mod p)
+    //   z0 x0 < 2^128;  z0 x0 = (z0 x0 >> 89) + (z0 x0 mod 2^89)  (mod p)
+    //   S = sum of those six terms + a < 2^91
+    __device__ static __forceinline__ u128 mul_add(u128 z, u128 x, u128 a) {
+        const u64 z0 = (u64)z, z1 = (u64)(z >> 64);
+        const u64 x0 = (u64)x, x1 = (u64)(x >> 64);
+        const u128 p00 = (u128)z0 * x0;
+        const u128 T = (u128)z1 * x0 + (u128)z0 * x1;
+        const u128 p11 = (u128)(z1 * x1);  // < 2^51, fits 64 bits
+        u128 S = (p11 << 39) + (T >> 25) + ((T & ((((u128)1) << 25) - 1)) << 64) + (p00 >> 89) +
+                 (p00 & Pv()) + a;
+        return (S & Pv()) + (S >> 89);
+    }
+
+    __device__ static __forceinline__ u32 bucket(u128 h, u32 mask) { return (u32)h & mask; }
+    __device__ static __forceinline__ u32 sign_bit(u128 h) { return (u32)(h >> 88) & 1u; }
+};
+
+// ------------------------------------------------------------ p = 2^64-59
+//
+// Pseudo-Mersenne: reduction by Algorithm division-generalized (3 steps, which
+// covers every v < (2^64/59)^2 (2^64 - 59), i.e. all v < 2^128 by the theorem
+// of Sec. 4) and Algorithm mod-generalized.  Values are canonical (< p).
+struct P64 {
+    static constexpr int B = 64;
+    static constexpr u64 C = 59;
+    static constexpr u64 P = 0xFFFFFFFFFFFFFFC5ull;  // 2^64 - 59
+    typedef u64 key_t;
+    typedef u64 val_t;
+
+    // x < 2^64 < 2p
+    __device__ static __forceinline__ u64 reduce_key(u64 x) { return x >= P ? x - P : x; }
+
+    // v mod p for v <= (p-1)^2 + (p-1) (a product of residues plus a residue):
+    //   v' = v + c < 2^128 (no carry out: (p-1)p + c < 2^128 - 2^70)
+    //   z  = v' >> 64;  z = (z c + v') >> 64  (twice)   -> floor(v / p) < 2^64
+    //   y  = (v + z c) mod 2^64                          -> v mod p
+    __device__ static __forceinline__ u64 mod_p(u128 v) {
+        const u128 vp = v + C;
+        u64 z = (u64)(vp >> 64);
+        z = (u64)(((u128)z * C + vp) >> 64);
+        z = (u64)(((u128)z * C + vp) >> 64);
+        return (u64)v + z * C;
+    }
+
+    __device__ static __forceinline__ u64 mul_add(u64 z, u64 x, u64 a) {
+        return mod_p((u128)z * x + a);
+    }
+
+    __device__ static __forceinline__ u32 bucket(u64 h, u32 mask) { return (u32)h & mask; }
+    __device__ static __forceinline__ u32 sign_bit(u64 h) { return (u32)(h >> 63); }
+};
+
+}  // namespace msf

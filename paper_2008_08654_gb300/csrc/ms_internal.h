@@ -1,0 +1,46 @@
+// Internal host-side state of the library's handles.  Not installed.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "ms.h"
+#include "ms_kernels.h"
+
+// A forced launch configuration (fields < 0 or == 0 mean "choose").
+struct LaunchOverride {
+    int place = -1;
+    int strategy = -1;
+    int threads = 0;
+    int blocks = 0;
+    int blocks_per_sm = 0;
+    int cluster = 0;
+};
+
+struct cs_sketch {
+    int t, k, b, mode, prime, log2m;
+    uint32_t m;
+    uint64_t c;
+    std::vector<msk::u64> words;  // host copy of the coefficients (limbs)
+    void* block = nullptr;        // single device allocation holding everything below
+    long long* counters = nullptr;    // t * m int64
+    msk::u64* coef_dev = nullptr;     // device copy of `words`
+    ms_u128* f2_partial = nullptr;    // F2 scratch: t * f2_splits partial sums
+    msk::u32* f2_ticket = nullptr;    // F2 scratch: completion ticket
+    int f2_splits = 1;
+    LaunchOverride launch;
+    msk::LaunchCfg last_cfg = {};
+    int last_specialized = 0;
+};
+
+namespace msi {
+int prime_id(int b, uint64_t c);
+int words_per_value(int prime);
+size_t key_bytes(int prime);
+bool less_than_p(msk::u64 lo, msk::u64 hi, int b, uint64_t c);
+void draw_uniform_below_p(int b, uint64_t c, uint64_t seed, int nvals, msk::u64* out);
+ms_status dev_alloc(void** p, size_t bytes);
+ms_status choose_update_config(const cs_sketch* sk, uint64_t n, msk::UpdateArgs& a,
+                               msk::LaunchCfg& cfg);
+}  // namespace msi

@@ -1,0 +1,114 @@
+// Internal interface between the host ABI code (ms_host.cu) and the kernel
+// translation units.  Not installed; the public interface is include/ms.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ms.h"
+
+namespace msk {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// Prime identifiers (p = 2^b - c).
+enum PrimeId { PRIME_31 = 0, PRIME_61 = 1, PRIME_89 = 2, PRIME_64_59 = 3 };
+
+// Counter placement of the update kernel.
+enum Place {
+    PLACE_SMEM = 0,   // whole t x m int32 tile in each block's shared memory
+    PLACE_DSMEM = 1,  // tile split over a thread-block cluster (distributed smem)
+    PLACE_GLOBAL = 2  // int64 atomics straight into the counters in HBM/L2
+};
+
+// Row-hash evaluation strategy (both give the same canonical value).
+enum Strategy {
+    STRAT_HORNER = 0,    // Algorithm Mersenne, k-1 lazy multiply-add steps per row
+    STRAT_POWER_SUM = 1  // x^2..x^(k-1) once per key, then sum a_i x^i per row
+};
+
+constexpr int MAX_T = 15;
+constexpr int MAX_K = 8;
+constexpr int MAX_COEF_WORDS = MAX_T * 2 * MAX_K * 2;  // t * functions * k * limbs
+
+struct UpdateArgs {
+    const void* keys;
+    const int32_t* weights;  // NULL: unit weights
+    u64 n;
+    long long* counters;     // t * m int64, row-major
+    const u64* coef_dev;     // device copy of the coefficients (generic kernels)
+    int t, k, log2m, mode;
+    int cluster_log2;        // DSMEM: log2(cluster size)
+    int vec_ok;              // keys and weights are 16-byte aligned
+    u32 w_safe;              // |w| <= w_safe may use int32 tile counters
+};
+
+// Launch configuration chosen on the host.
+struct LaunchCfg {
+    int place;
+    int strategy;
+    int threads;
+    int blocks;       // total blocks (a multiple of the cluster size)
+    int cluster;      // 1 unless PLACE_DSMEM
+    size_t smem;      // dynamic shared memory bytes
+};
+
+// Returns cudaSuccess or the launch error.  `specialized` is set to whether a
+// compile-time (t, k) specialization served the call.
+// coef_host: the sketch's coefficient limbs (function-major, a_0 first).
+cudaError_t launch_cs_update(int prime, const UpdateArgs& a, const u64* coef_host,
+                             const LaunchCfg& cfg, cudaStream_t stream, int* specialized);
+
+// Occupancy query for a configuration: resident blocks per SM (SMEM/GLOBAL)
+// or co-resident clusters on the device (DSMEM).
+cudaError_t query_cs_update_occupancy(int prime, const UpdateArgs& a, const u64* coef_host,
+                                      const LaunchCfg& cfg, int* result);
+
+// Per-prime entry points (one translation unit each).
+cudaError_t launch_update_p31(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                              cudaStream_t stream, int* specialized, int* occupancy);
+cudaError_t launch_update_p61(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                              cudaStream_t stream, int* specialized, int* occupancy);
+cudaError_t launch_update_p89(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                              cudaStream_t stream, int* specialized, int* occupancy);
+cudaError_t launch_update_p64(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                              cudaStream_t stream, int* specialized, int* occupancy);
+
+struct F2Args {
+    const long long* counters;
+    int t;
+    u32 m;
+    int splits;          // blocks per row (power of two, divides m)
+    ms_u128* partial;    // t * splits scratch
+    u32* ticket;         // scratch counter, zero between launches
+    ms_u128* out;        // median
+    ms_u128* rows;       // optional t row values
+};
+cudaError_t launch_cs_f2(const F2Args& a, int threads, cudaStream_t stream);
+
+struct QueryArgs {
+    const void* keys;
+    u64 n;
+    const long long* counters;
+    const u64* coef_dev;
+    int t, k, log2m, mode;
+    long long* out;
+};
+cudaError_t launch_cs_point_query(int prime, const QueryArgs& a, cudaStream_t stream);
+
+cudaError_t launch_add_counters(long long* dst, const long long* src, u64 n, cudaStream_t stream);
+cudaError_t launch_zero(void* dst, u64 bytes, cudaStream_t stream);
+
+struct HashCoef {
+    u64 w[MAX_K * 2];  // k coefficients, 1 or 2 limbs each
+};
+cudaError_t launch_hash_eval(int prime, const void* keys, void* out, u64 n, int k,
+                             const HashCoef& coef, bool vec, cudaStream_t stream);
+
+cudaError_t launch_divmod(int prime, const ms_u128* v, ms_u128* q, void* r, u64 n,
+                          cudaStream_t stream);
+
+cudaError_t run_probe_mul128(int variant, int iters, u64* sink, double* rate, double* ms);
+
+}  // namespace msk

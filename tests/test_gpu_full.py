@@ -1,0 +1,53 @@
+"""Full-size GPU parity in the launch configuration bench.py times.
+
+The large single sketch (2^28 Zipf keys, t=7, m=2^16, unit weights) and the
+plain sketch (2^20 uniform keys, weights in [-100, 100], t=5, m=1024) are run
+through cs_update with the library's automatic launch choice -- exactly what
+bench.py does -- and every counter and the F2 estimate are compared with the
+multi-threaded CPU oracle over the whole stream.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+NTHREADS = max(1, os.cpu_count() or 1)
+
+
+def _run(workload, seed=2008, n=None):
+    import torch
+
+    import bench
+    import paper_2008_08654_gb300 as ms
+    wl = bench.WORKLOADS[workload]
+    keys, w = bench.make_inputs(wl, seed, 0, n)
+    sk = ms.Sketch(t=wl["t"], m=wl["m"], k=4, b=61, c=1, seed=seed, mode=wl["mode"])
+    sk.update(torch.from_numpy(keys.view(np.int64)).cuda(),
+              None if w is None else torch.from_numpy(w).cuda())
+    got_c = sk.counters().cpu().numpy()
+    got_f2 = sk.f2()
+    launch = sk.last_launch()
+    coeffs = oracle.sketch_coeffs(61, 1, 4, wl["t"], wl["mode"], seed)
+    want_c = oracle.cs_update(61, 1, 4, wl["t"], wl["m"], wl["mode"], coeffs, keys, w,
+                              nthreads=NTHREADS)
+    assert np.array_equal(got_c, want_c), "%d counters differ" % int((got_c != want_c).sum())
+    assert got_f2 == oracle.f2_estimate(want_c)
+    return launch
+
+
+def test_plain_sketch_full_size():
+    _run("plain")
+
+
+def test_large_sketch_full_size():
+    launch = _run("large")
+    print("large sketch launch:", launch)
+
+
+def test_large_sketch_two_poly_quarter():
+    """Two polynomials per row on the first 2^26 keys of the same stream."""
+    _run("large-twopoly", n=1 << 26)
