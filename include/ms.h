@@ -229,22 +229,31 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  * (place, strategy) or == 0 (the others) keeps the library's own choice.
  *  place:    0 = int32 tile in each block's shared memory, 1 = tile split
  *            over a thread-block cluster's distributed shared memory,
- *            2 = int64 atomics straight into the counters.
+ *            2 = global memory: int32 replicas of the counters (block b adds
+ *            into replica b mod R, then one kernel adds the replicas into the
+ *            int64 counters; sketches whose tile exceeds 112 KiB own R <= 8
+ *            replicas, others fall back to 3), 3 = int64 atomics straight
+ *            into the counters.
+ *  Default: 0 when the t*m int32 tile fits 112 KiB, else 2.
  *  strategy: 0 = Horner per row (Algorithm Mersenne), 1 = powers of x once per
  *            key, then sum a_i x^i per row (only for p = 2^61-1 with k = 4;
  *            other sketches use Horner).  Both give identical hash values.
  *  threads (multiple of 32, <= 512), blocks (total), blocks_per_sm (cap),
- *  cluster (power of two <= 16, place 1 only).
+ *  cluster (power of two <= 16, place 1 only), replicas (power of two <= 32,
+ *  place 2 only; capped at the replicas the sketch owns; default 32),
+ *  aggregate (0/1, default 1: with unit weights and place 2 or 3, lanes of a
+ *  warp holding the same key send one atomic carrying their count; every key
+ *  is still hashed).
  * Errors: INVALID_ARG.
  */
 ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int threads, int blocks,
-                        int blocks_per_sm, int cluster);
+                        int blocks_per_sm, int cluster, int replicas, int aggregate);
 
 /* The configuration the most recent cs_update on this sketch launched with;
  * `specialized` is 1 when a compile-time (t, k) kernel served it.  Any output
  * pointer may be NULL. */
 ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* threads, int* blocks,
-                         int* cluster, int* smem, int* specialized);
+                         int* cluster, int* smem, int* specialized, int* replicas);
 
 /* ---------------------------------------------------- integer-pipe peak probe */
 
@@ -256,6 +265,8 @@ ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* th
  * (8 bytes) receives a checksum so the work cannot be elided.  Synchronous.
  *  variant 0: full 64x64->128 product (low 64 bits and __umul64hi).
  *  variant 1: one 32x32->64 multiply-add (the partial product it is built of).
+ *  variant 2: one 32-bit multiply-add (low word only).
+ *  variant 3: one 32-bit three-input integer add (the integer ALU pipe).
  */
 ms_status ms_probe_mul128(int variant, int iters, uint64_t* sink_dev, double* rate, double* ms);
 

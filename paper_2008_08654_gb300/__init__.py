@@ -84,9 +84,17 @@ def _load():
         "cs_merge": (i, [vp, vp, vp]),
         "cs_export": (i, [vp, vp, ctypes.POINTER(sz), vp]),
         "cs_import": (i, [pp, vp, sz]),
-        "cs_set_launch": (i, [vp, i, i, i, i, i, i]),
-        "cs_last_launch": (i, [vp, ip, ip, ip, ip, ip, ip, ip]),
+        "cs_set_launch": (i, [vp, i, i, i, i, i, i, i, i]),
+        "cs_last_launch": (i, [vp, ip, ip, ip, ip, ip, ip, ip, ip]),
         "ms_probe_mul128": (i, [i, i, vp, dbl, dbl]),
+        "cs_batch_default_tuning": (i, [vp]),
+        "cs_batch_create": (i, [pp, vp, i, vp, vp]),
+        "cs_batch_launch": (i, [vp, vp]),
+        "cs_batch_launch_direct": (i, [vp, vp]),
+        "cs_batch_destroy": (i, [vp]),
+        "cs_batch_info": (i, [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ip, ip,
+                              ctypes.POINTER(sz)]),
+        "cs_batch_tune": (i, [vp, i, vp, i, i, vp, ctypes.POINTER(ctypes.c_double), vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -334,14 +342,16 @@ class Sketch:
         return cls(_handle=h)
 
     def set_launch(self, place: int = -1, strategy: int = -1, threads: int = 0, blocks: int = 0,
-                   blocks_per_sm: int = 0, cluster: int = 0):
+                   blocks_per_sm: int = 0, cluster: int = 0, replicas: int = 0,
+                   aggregate: int = -1):
         _check(_load().cs_set_launch(self._h, place, strategy, threads, blocks, blocks_per_sm,
-                                     cluster), "cs_set_launch")
+                                     cluster, replicas, aggregate), "cs_set_launch")
 
     def last_launch(self) -> dict:
-        v = [ctypes.c_int() for _ in range(7)]
+        v = [ctypes.c_int() for _ in range(8)]
         _check(_load().cs_last_launch(self._h, *[ctypes.byref(x) for x in v]), "cs_last_launch")
-        keys = ("place", "strategy", "threads", "blocks", "cluster", "smem", "specialized")
+        keys = ("place", "strategy", "threads", "blocks", "cluster", "smem", "specialized",
+                "replicas")
         return dict(zip(keys, [x.value for x in v]))
 
     def __del__(self):
@@ -364,3 +374,94 @@ def probe_mul128(variant: int = 0, iters: int = 4096) -> tuple:
     _check(_load().ms_probe_mul128(variant, iters, _ptr(sink), ctypes.byref(rate),
                                    ctypes.byref(ms)), "ms_probe_mul128")
     return rate.value, ms.value
+
+
+# ------------------------------------------------------------------ batched
+
+class BatchJob(ctypes.Structure):
+    _fields_ = [("sketch", ctypes.c_void_p), ("keys_dev", ctypes.c_void_p),
+                ("weights_dev", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("chunk_keys", ctypes.c_uint32), ("smem_min_ratio", ctypes.c_uint32),
+                ("rows_per_item", ctypes.c_int), ("strategy", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "BatchTuning":
+        t = default_tuning()
+        for k, v in d.items():
+            setattr(t, k, v)
+        return t
+
+
+def default_tuning() -> BatchTuning:
+    t = BatchTuning()
+    _check(_load().cs_batch_default_tuning(ctypes.byref(t)), "cs_batch_default_tuning")
+    return t
+
+
+def _job_array(jobs):
+    arr = (BatchJob * len(jobs))()
+    keep = []
+    for j, (sk, keys, w) in enumerate(jobs):
+        n = _nkeys(keys, sk.b, sk.c)
+        arr[j].sketch = sk.handle
+        arr[j].keys_dev = _ptr(keys) if n else None
+        arr[j].weights_dev = _ptr(w) if w is not None else None
+        arr[j].n = n
+        keep.append((sk, keys, w))
+    return arr, keep
+
+
+class Batch:
+    """One persistent, graph-captured launch over many (sketch, keys, weights)
+    jobs (cs_batch_*).  The tensors and sketches must outlive the plan."""
+
+    def __init__(self, jobs, tuning: BatchTuning | dict | None = None):
+        arr, self._keep = _job_array(jobs)
+        if isinstance(tuning, dict):
+            tuning = BatchTuning.from_dict(tuning)
+        h = ctypes.c_void_p()
+        _check(_load().cs_batch_create(ctypes.byref(h), arr, len(jobs),
+                                       ctypes.byref(tuning) if tuning is not None else None,
+                                       None), "cs_batch_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_load().cs_batch_launch(self._h, _stream(stream)), "cs_batch_launch")
+
+    def launch_direct(self, stream=None):
+        _check(_load().cs_batch_launch_direct(self._h, _stream(stream)), "cs_batch_launch_direct")
+
+    def info(self) -> dict:
+        tk, ti = ctypes.c_uint64(), ctypes.c_uint32()
+        bl, th, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(_load().cs_batch_info(self._h, ctypes.byref(tk), ctypes.byref(ti), ctypes.byref(bl),
+                                     ctypes.byref(th), ctypes.byref(sm)), "cs_batch_info")
+        return {"total_keys": tk.value, "total_items": ti.value, "blocks": bl.value,
+                "threads": th.value, "smem": sm.value}
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.cs_batch_destroy(self._h)
+            self._h = None
+
+
+def tune_batched(jobs, candidates, reps: int = 3, stream=None):
+    """Times every candidate tuning (dicts or BatchTuning) on the real jobs;
+    returns (best tuning as a dict, list of median ms per candidate; -1 when a
+    candidate could not launch).  Counters are left as they were."""
+    arr, keep = _job_array(jobs)
+    cands = (BatchTuning * len(candidates))()
+    for i, c in enumerate(candidates):
+        cands[i] = BatchTuning.from_dict(c) if isinstance(c, dict) else c
+    best = BatchTuning()
+    times = (ctypes.c_double * len(candidates))()
+    _check(_load().cs_batch_tune(arr, len(jobs), cands, len(candidates), reps, ctypes.byref(best),
+                                 times, _stream(stream)), "cs_batch_tune")
+    return best.as_dict(), list(times)

@@ -212,6 +212,29 @@ cudaError_t launch_add_counters(long long* dst, const long long* src, u64 n, cud
     return cudaGetLastError();
 }
 
+__global__ void k_reduce_replicas(long long* __restrict__ counters, int* __restrict__ rep, int nrep,
+                                  u64 cells) {
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < cells;
+         i += (u64)gridDim.x * blockDim.x) {
+        long long s = 0;
+        for (int r = 0; r < nrep; ++r) {
+            int* p = rep + (u64)r * cells + i;
+            s += (long long)*p;
+            *p = 0;
+        }
+        if (s != 0) counters[i] = (long long)((u64)counters[i] + (u64)s);
+    }
+}
+
+cudaError_t launch_reduce_replicas(long long* counters, int* replicas, int nrep, u64 cells,
+                                   cudaStream_t stream) {
+    if (cells == 0 || nrep < 1) return cudaSuccess;
+    u64 blocks = (cells + 255) / 256;
+    if (blocks > 152ull * 8) blocks = 152ull * 8;
+    k_reduce_replicas<<<(unsigned)blocks, 256, 0, stream>>>(counters, replicas, nrep, cells);
+    return cudaGetLastError();
+}
+
 __global__ void k_zero(uint4* dst, u64 n16, unsigned char* tail, u64 ntail) {
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
@@ -381,6 +404,8 @@ cudaError_t launch_divmod(int prime, const ms_u128* v, ms_u128* q, void* r, u64 
 // folded into one checksum so nothing can be removed.
 //  variant 0: a <- lo(a*b) ^ hi(a*b), a full 64x64->128 product per step
 //  variant 1: a <- lo32(a) * b32 + a, one 32x32->64 multiply-add per step
+//  variant 2: x <- x * b32 + c, one 32-bit multiply-add (low word) per step
+//  variant 3: x <- x + b32 + y, one 32-bit three-input add per step
 __global__ void __launch_bounds__(256) k_probe(int variant, int iters, u64 seed, u64* sink) {
     u64 a[8];
     const u64 b = seed | 1ull;
@@ -392,11 +417,31 @@ __global__ void __launch_bounds__(256) k_probe(int variant, int iters, u64 seed,
 #pragma unroll
             for (int c = 0; c < 8; ++c) a[c] = (a[c] * b) ^ __umul64hi(a[c], b);
         }
-    } else {
+    } else if (variant == 1) {
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) a[c] = (u64)(u32)a[c] * b32 + a[c];
         }
+    } else if (variant == 2) {  // 32-bit multiply-add (low word only)
+        u32 x[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = (u32)a[c];
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[c] = x[c] * b32 + (u32)c;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = x[c];
+    } else {  // variant 3: 32-bit three-input add (integer ALU)
+        u32 x[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = (u32)a[c];
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[c] = x[c] + b32 + x[(c + 1) & 7];
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = x[c];
     }
     u64 s = 0;
 #pragma unroll

@@ -219,6 +219,16 @@ __device__ __forceinline__ void load_weights4(const int32_t* w, u64 j, u64 n, bo
     }
 }
 
+// ------------------------------------------------------------ warp matching
+
+// Mask of the lanes of this (converged) warp that hold the same key.
+__device__ __forceinline__ u32 match_key(u64 k) { return __match_any_sync(0xffffffffu, k); }
+__device__ __forceinline__ u32 match_key(u32 k) { return __match_any_sync(0xffffffffu, k); }
+__device__ __forceinline__ u32 match_key(const u128x& k) {
+    // equal keys have equal limbs: intersect the two limb matches
+    return __match_any_sync(0xffffffffu, k.lo) & __match_any_sync(0xffffffffu, k.hi);
+}
+
 // ------------------------------------------------------------ cluster helpers
 
 __device__ __forceinline__ u32 cluster_rank() {
@@ -247,18 +257,22 @@ __device__ __forceinline__ void global_add64(long long* p, long long v) {
 
 // ------------------------------------------------------------ the kernel
 
-// One counter update: C[row][bucket] += (sign ? -w : w).
+// One counter update: C[row][bucket] += (sign ? -w : w).  For PLACE_GLOBAL,
+// `tile` is this block's int32 replica of the counters in global memory (or
+// NULL: int64 atomics on the counters themselves).
 template <int PLACE>
 __device__ __forceinline__ void apply_update(int* tile, u32 tile_saddr, long long* counters,
                                              int row, u32 bucket, u32 sign, int w, bool big,
                                              u32 m, int log2m, int lcs) {
-    if (PLACE == PLACE_GLOBAL || big) {
+    if (big || (PLACE == PLACE_GLOBAL && tile == nullptr)) {
         const long long d = sign ? -(long long)w : (long long)w;
         global_add64(counters + (((u64)row) << log2m) + bucket, d);
         return;
     }
     const int d = sign ? -w : w;
-    if (PLACE == PLACE_SMEM) {
+    if (PLACE == PLACE_GLOBAL) {
+        atomicAdd(tile + (row << log2m) + bucket, d);  // red.global.add.s32 on the replica
+    } else if (PLACE == PLACE_SMEM) {
         atomicAdd(tile + (row << log2m) + bucket, d);
     } else {  // PLACE_DSMEM: owner block = high bits of the bucket
         const int lshift = log2m - lcs;
@@ -289,12 +303,17 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
     const int lcs = (PLACE == PLACE_DSMEM) ? a.cluster_log2 : 0;
     const u32 mloc = m >> lcs;
 
-    int* tile = reinterpret_cast<int*>(smem);
+    // PLACE_GLOBAL: `tile` is this block's replica in global memory (or NULL)
+    int* tile = (PLACE == PLACE_GLOBAL)
+                    ? (a.replicas ? a.replicas + (size_t)(blockIdx.x & a.replica_mask) * ((u32)t << log2m)
+                                  : nullptr)
+                    : reinterpret_cast<int*>(smem);
     const u32 tile_cells = (PLACE == PLACE_GLOBAL) ? 0u : (u32)t * mloc;
     u64* scoef = reinterpret_cast<u64*>(smem + (size_t)tile_cells * 4u);
-    const u32 tile_saddr = (u32)__cvta_generic_to_shared(tile);
+    const u32 tile_saddr = (PLACE == PLACE_GLOBAL) ? 0u : (u32)__cvta_generic_to_shared(tile);
 
-    for (u32 i = threadIdx.x; i < tile_cells; i += blockDim.x) tile[i] = 0;
+    if (PLACE != PLACE_GLOBAL)
+        for (u32 i = threadIdx.x; i < tile_cells; i += blockDim.x) tile[i] = 0;
     if (GENERIC) {
         const int nw = t * NF * k * W;
         for (int i = threadIdx.x; i < nw; i += blockDim.x) scoef[i] = a.coef_dev[i];
@@ -309,11 +328,29 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
     const bool vec = a.vec_ok != 0;
     const u32 w_safe = a.w_safe;
     const u64 stride = (u64)gridDim.x * blockDim.x * 4ull;
-    for (u64 j = ((u64)blockIdx.x * blockDim.x + threadIdx.x) * 4ull; j < n; j += stride) {
+    // The loop runs on the warp's first key index, so every lane of a warp takes
+    // the same number of iterations (lanes past the end load weight-0 keys);
+    // warp-wide matching below relies on it.
+    const u64 lane4 = (u64)(threadIdx.x & 31u) * 4ull;
+    for (u64 jw = ((u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * 4ull; jw < n;
+         jw += stride) {
+        const u64 j = jw + lane4;
         typename Ops::key_t key[4];
         int wt[4];
         KeyIO<F>::load(a.keys, j, n, vec, key);
         load_weights4(a.weights, j, n, vec, wt);
+        if (PLACE == PLACE_GLOBAL && a.aggregate && a.weights == nullptr) {
+            // Unit weights: lanes of this warp holding the same key would add
+            // to the same t counters.  The lowest such lane adds the group's
+            // count; the others still hash their key but add nothing.
+            const u32 lane = threadIdx.x & 31u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const u32 valid = __ballot_sync(0xffffffffu, wt[q] != 0);
+                u32 grp = match_key(key[q]) & valid;
+                if (wt[q] != 0) wt[q] = ((grp & ((1u << lane) - 1u)) == 0u) ? __popc(grp) : 0;
+            }
+        }
         bool big[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {

@@ -19,13 +19,26 @@ using msk::u32;
 using msk::u64;
 
 namespace {
-
 thread_local char g_cuda_err[256] = "";
+}  // namespace
 
-ms_status cuda_fail(cudaError_t e, const char* where) {
+// Records the failing call for ms_last_cuda_error() and clears the sticky
+// runtime error state where that is possible.
+ms_status msi::cuda_fail(cudaError_t e, const char* where) {
     snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+    cudaGetLastError();
     return MS_ERR_CUDA;
 }
+
+using msi::cuda_fail;
+
+// Largest int32 counter tile kept in one block's shared memory by default
+// (two such blocks fit an SM).
+static const size_t kSmemTileBudget = 112 * 1024;
+static const int kMaxReplicas = 32;   // replicas a large sketch owns (<= 64 MiB)
+static const int kDefaultReplicas = 32;  // replicas a default launch uses
+
+namespace {
 
 #define MS_CUDA(call, where)                              \
     do {                                                  \
@@ -337,12 +350,26 @@ static ms_status sketch_make(cs_sketch** out, int t, uint32_t m, int k, int b, u
     sk->f2_splits = 1;
     while (sk->f2_splits < 64 && (m / (uint32_t)(sk->f2_splits * 2)) >= 4096) sk->f2_splits *= 2;
 
-    // one device block: counters | coefficients | F2 partials | F2 ticket
+    // Sketches whose int32 tile does not fit the shared-memory budget update
+    // through R int32 replicas in global memory (R a power of two <= 32, at
+    // most 64 MiB of replicas): block b adds into replica b mod R, which splits
+    // the atomic traffic on a hot counter R ways.
+    const size_t tile_bytes = (size_t)t * m * 4;
+    int nrep = 0;
+    if (tile_bytes > kSmemTileBudget) {
+        nrep = kMaxReplicas;
+        while (nrep > 1 && (size_t)nrep * tile_bytes > (64ull << 20)) nrep /= 2;
+        if ((size_t)nrep * tile_bytes > (64ull << 20)) nrep = 0;
+    }
+    sk->nrep = nrep;
+
+    // one device block: counters | coefficients | F2 partials | F2 ticket | replicas
     const size_t counters_bytes = (size_t)t * m * 8;
     const size_t coef_off = (counters_bytes + 255) / 256 * 256;
     const size_t part_off = coef_off + (nwords * 8 + 255) / 256 * 256;
     const size_t ticket_off = part_off + ((size_t)t * sk->f2_splits * 16 + 255) / 256 * 256;
-    const size_t total = ticket_off + 256;
+    const size_t rep_off = ticket_off + 256;
+    const size_t total = rep_off + (size_t)nrep * tile_bytes;
     void* blk = nullptr;
     ms_status st = dev_alloc(&blk, total);
     if (st != MS_OK) {
@@ -354,9 +381,11 @@ static ms_status sketch_make(cs_sketch** out, int t, uint32_t m, int k, int b, u
     sk->coef_dev = (u64*)((char*)blk + coef_off);
     sk->f2_partial = (ms_u128*)((char*)blk + part_off);
     sk->f2_ticket = (u32*)((char*)blk + ticket_off);
+    sk->replicas = nrep ? (int*)((char*)blk + rep_off) : nullptr;
     cudaError_t e = cudaMemcpy(sk->coef_dev, sk->words.data(), nwords * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(sk->counters, 0, counters_bytes);
     if (e == cudaSuccess) e = cudaMemset(sk->f2_ticket, 0, 256);
+    if (e == cudaSuccess && nrep) e = cudaMemset(sk->replicas, 0, (size_t)nrep * tile_bytes);
     if (e != cudaSuccess) {
         sketch_free_device(sk);
         delete sk;
@@ -455,14 +484,12 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::Update
     cfg.strategy = ov.strategy >= 0 ? ov.strategy : msk::STRAT_POWER_SUM;
     cfg.cluster = 1;
     int place = ov.place;
-    if (place < 0) {
-        if (tile_bytes + extra <= 112 * 1024)
-            place = msk::PLACE_SMEM;
-        else if (tile_bytes / 16 + extra <= optin)
-            place = msk::PLACE_DSMEM;
-        else
-            place = msk::PLACE_GLOBAL;
+    bool direct = false;  // PLACE_GLOBAL without replicas
+    if (place == 3) {
+        place = msk::PLACE_GLOBAL;
+        direct = true;
     }
+    if (place < 0) place = (tile_bytes + extra <= kSmemTileBudget) ? msk::PLACE_SMEM : msk::PLACE_GLOBAL;
     if (place == msk::PLACE_SMEM && tile_bytes + extra > optin) place = msk::PLACE_GLOBAL;
     if (place == msk::PLACE_DSMEM) {
         int cl = ov.cluster > 0 ? ov.cluster : 0;
@@ -479,6 +506,12 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::Update
             cfg.cluster = cl;
     }
     cfg.place = place;
+    cfg.replicas = 0;
+    if (place == msk::PLACE_GLOBAL && !direct && sk->nrep > 0) {
+        int r = ov.replicas > 0 ? ov.replicas : kDefaultReplicas;
+        if (r > sk->nrep) r = sk->nrep;
+        cfg.replicas = r;
+    }
     int lcs = 0;
     while ((1 << lcs) < cfg.cluster) ++lcs;
     cfg.smem = (place == msk::PLACE_GLOBAL ? 0 : tile_bytes / cfg.cluster) + extra;
@@ -491,6 +524,9 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::Update
     a.coef_dev = sk->coef_dev;
     a.counters = sk->counters;
     a.n = n;
+    a.replicas = cfg.replicas ? sk->replicas : nullptr;
+    a.replica_mask = cfg.replicas ? (u32)(cfg.replicas - 1) : 0u;
+    a.aggregate = ov.aggregate >= 0 ? ov.aggregate : 1;
 
     // resident capacity (the cluster query needs a grid that is a whole cluster)
     cfg.blocks = cfg.cluster;
@@ -504,7 +540,10 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::Update
         cfg.cluster = 1;
         cfg.smem = extra;
         cfg.blocks = 1;
+        cfg.replicas = sk->nrep < kDefaultReplicas ? sk->nrep : kDefaultReplicas;
         a.cluster_log2 = 0;
+        a.replicas = cfg.replicas ? sk->replicas : nullptr;
+        a.replica_mask = cfg.replicas ? (u32)(cfg.replicas - 1) : 0u;
         e = msk::query_cs_update_occupancy(sk->prime, a, sk->words.data(), cfg, &occ);
         if (e != cudaSuccess || occ < 1) return cuda_fail(e, "occupancy");
     }
@@ -532,16 +571,21 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::Update
     if (cfg.place == msk::PLACE_DSMEM) blocks = (blocks + cfg.cluster - 1) / cfg.cluster * cfg.cluster;
     cfg.blocks = (int)blocks;
 
-    // int32 tile counters: the most keys any one tile can see, times |w|
+    // int32 tile/replica counters: the most keys any one of them can see, times |w|
     const u64 iters = (n + (u64)blocks * per_iter - 1) / ((u64)blocks * per_iter);
-    const u64 per_tile = iters * per_iter * (u64)cfg.cluster;
+    u64 per_tile = iters * per_iter * (u64)cfg.cluster;
+    if (cfg.place == msk::PLACE_GLOBAL && cfg.replicas)
+        per_tile = iters * per_iter * (((u64)blocks + cfg.replicas - 1) / cfg.replicas);
     a.w_safe = per_tile >= 0x7FFFFFFFull ? 0u : (u32)(0x7FFFFFFFull / (per_tile ? per_tile : 1));
-    if (per_tile >= 0x7FFFFFFFull && cfg.place != msk::PLACE_GLOBAL) {
-        // even unit weights could overflow an int32 tile counter
+    if (per_tile >= 0x7FFFFFFFull && (cfg.place != msk::PLACE_GLOBAL || cfg.replicas)) {
+        // even unit weights could overflow an int32 counter: int64 atomics only
         cfg.place = msk::PLACE_GLOBAL;
         cfg.cluster = 1;
         cfg.smem = extra;
+        cfg.replicas = 0;
         a.cluster_log2 = 0;
+        a.replicas = nullptr;
+        a.replica_mask = 0;
     }
     return MS_OK;
 }
@@ -565,6 +609,10 @@ extern "C" ms_status cs_update(cs_sketch* sk, const void* keys_dev, const int32_
     int spec = 0;
     MS_CUDA(msk::launch_cs_update(sk->prime, a, sk->words.data(), cfg, (cudaStream_t)stream, &spec),
             "cs_update");
+    if (a.replicas)
+        MS_CUDA(msk::launch_reduce_replicas(sk->counters, sk->replicas, cfg.replicas,
+                                            (u64)sk->t * sk->m, (cudaStream_t)stream),
+                "cs_update replicas");
     sk->last_cfg = cfg;
     sk->last_specialized = spec;
     return MS_OK;
@@ -712,33 +760,41 @@ extern "C" ms_status cs_import(cs_sketch** out, const void* buf_host, size_t siz
 // Tuning hook: force a launch configuration for later cs_update calls on this
 // sketch (any field < 0 or 0 keeps the automatic choice).
 extern "C" ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int threads, int blocks,
-                                   int blocks_per_sm, int cluster) {
+                                   int blocks_per_sm, int cluster, int replicas, int aggregate) {
     if (!sk) return MS_ERR_INVALID_ARG;
-    if (place > msk::PLACE_GLOBAL || strategy > msk::STRAT_POWER_SUM) return MS_ERR_INVALID_ARG;
+    if (place > 3 || strategy > msk::STRAT_POWER_SUM) return MS_ERR_INVALID_ARG;
     if (threads != 0 && threads != -1 &&
         (threads < 32 || threads > 512 || threads % 32 != 0))
         return MS_ERR_INVALID_ARG;
     if (cluster > 16 || (cluster > 0 && (cluster & (cluster - 1)) != 0)) return MS_ERR_INVALID_ARG;
+    if (replicas > 32 || (replicas > 0 && (replicas & (replicas - 1)) != 0) || aggregate > 1)
+        return MS_ERR_INVALID_ARG;
     sk->launch.place = place;
     sk->launch.strategy = strategy;
     sk->launch.threads = threads;
     sk->launch.blocks = blocks;
     sk->launch.blocks_per_sm = blocks_per_sm;
     sk->launch.cluster = cluster;
+    sk->launch.replicas = replicas;
+    sk->launch.aggregate = aggregate;
     return MS_OK;
 }
 
 // The configuration the last cs_update on this sketch launched with.
 extern "C" ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* threads,
-                                    int* blocks, int* cluster, int* smem, int* specialized) {
+                                    int* blocks, int* cluster, int* smem, int* specialized,
+                                    int* replicas) {
     if (!sk) return MS_ERR_INVALID_ARG;
-    if (place) *place = sk->last_cfg.place;
+    if (place)
+        *place = (sk->last_cfg.place == msk::PLACE_GLOBAL && sk->last_cfg.replicas == 0)
+                     ? 3 : sk->last_cfg.place;
     if (strategy) *strategy = sk->last_cfg.strategy;
     if (threads) *threads = sk->last_cfg.threads;
     if (blocks) *blocks = sk->last_cfg.blocks;
     if (cluster) *cluster = sk->last_cfg.cluster;
     if (smem) *smem = (int)sk->last_cfg.smem;
     if (specialized) *specialized = sk->last_specialized;
+    if (replicas) *replicas = sk->last_cfg.replicas;
     return MS_OK;
 }
 
@@ -746,7 +802,7 @@ extern "C" ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strate
 
 extern "C" ms_status ms_probe_mul128(int variant, int iters, uint64_t* sink_dev, double* rate,
                                      double* ms) {
-    if (!sink_dev || !rate || !ms || iters < 1 || (variant != 0 && variant != 1))
+    if (!sink_dev || !rate || !ms || iters < 1 || variant < 0 || variant > 3)
         return MS_ERR_INVALID_ARG;
     MS_CUDA(msk::run_probe_mul128(variant, iters, (u64*)sink_dev, rate, ms), "ms_probe_mul128");
     return MS_OK;

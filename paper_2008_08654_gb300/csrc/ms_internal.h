@@ -16,6 +16,8 @@ struct LaunchOverride {
     int blocks = 0;
     int blocks_per_sm = 0;
     int cluster = 0;
+    int replicas = 0;    // PLACE_GLOBAL: use this many of the sketch's replicas
+    int aggregate = -1;  // warp aggregation of equal keys (unit weights, global placement)
 };
 
 struct cs_sketch {
@@ -29,12 +31,15 @@ struct cs_sketch {
     ms_u128* f2_partial = nullptr;    // F2 scratch: t * f2_splits partial sums
     msk::u32* f2_ticket = nullptr;    // F2 scratch: completion ticket
     int f2_splits = 1;
+    int* replicas = nullptr;          // update scratch: nrep int32 copies of the counters
+    int nrep = 0;                     // (large sketches only; zero between calls)
     LaunchOverride launch;
     msk::LaunchCfg last_cfg = {};
     int last_specialized = 0;
 };
 
 namespace msi {
+ms_status cuda_fail(cudaError_t e, const char* where);
 int prime_id(int b, uint64_t c);
 int words_per_value(int prime);
 size_t key_bytes(int prime);

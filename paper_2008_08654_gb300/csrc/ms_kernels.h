@@ -41,7 +41,11 @@ struct UpdateArgs {
     int t, k, log2m, mode;
     int cluster_log2;        // DSMEM: log2(cluster size)
     int vec_ok;              // keys and weights are 16-byte aligned
-    u32 w_safe;              // |w| <= w_safe may use int32 tile counters
+    u32 w_safe;              // |w| <= w_safe may use int32 tile/replica counters
+    int* replicas;           // PLACE_GLOBAL: R int32 copies of the t x m counters,
+                             // or NULL for direct int64 atomics
+    u32 replica_mask;        // R - 1 (R a power of two)
+    int aggregate;           // PLACE_GLOBAL, unit weights: merge equal keys of a warp
 };
 
 // Launch configuration chosen on the host.
@@ -51,6 +55,7 @@ struct LaunchCfg {
     int threads;
     int blocks;       // total blocks (a multiple of the cluster size)
     int cluster;      // 1 unless PLACE_DSMEM
+    int replicas;     // PLACE_GLOBAL: int32 replica count (0 = direct int64 atomics)
     size_t smem;      // dynamic shared memory bytes
 };
 
@@ -98,6 +103,11 @@ struct QueryArgs {
 cudaError_t launch_cs_point_query(int prime, const QueryArgs& a, cudaStream_t stream);
 
 cudaError_t launch_add_counters(long long* dst, const long long* src, u64 n, cudaStream_t stream);
+
+// counters[i] += sum_r replicas[r * cells + i] (sign-extended), then every
+// replica cell is zeroed for the next update.
+cudaError_t launch_reduce_replicas(long long* counters, int* replicas, int nrep, u64 cells,
+                                   cudaStream_t stream);
 cudaError_t launch_zero(void* dst, u64 bytes, cudaStream_t stream);
 
 struct HashCoef {

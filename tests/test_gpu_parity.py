@@ -163,20 +163,27 @@ CASES = [
     (61, 1, 7, 4096, 4, 0, -1, -1, "unit"),
     (61, 1, 7, 8192, 4, 1, 1, 1, "unit"),       # DSMEM, auto cluster
     (61, 1, 5, 4096, 4, 0, 1, 0, "pm100"),      # DSMEM
-    (61, 1, 5, 256, 4, 0, 2, 1, "pm100"),       # global atomics
+    (61, 1, 5, 256, 4, 0, 3, 1, "pm100"),       # int64 global atomics
+    (61, 1, 7, 65536, 4, 0, 2, 1, "pm100"),     # int32 global replicas (large sketch)
+    (61, 1, 7, 65536, 4, 1, 2, 0, "unit"),      # replicas, two-poly, Horner
+    (61, 1, 3, 1 << 20, 2, 0, -1, -1, "pm100"), # generic kernel, replicas
+    (61, 1, 1, 1 << 24, 4, 0, -1, -1, "unit"),  # m = 2^24 (maximum)
     (61, 1, 3, 64, 2, 0, -1, -1, "pm100"),      # generic kernel
     (61, 1, 3, 64, 2, 1, 1, -1, "pm100"),       # generic, DSMEM
     (61, 1, 1, 2, 8, 0, -1, -1, "pm100"),       # m = 2, k = 8
     (61, 1, 15, 128, 1, 0, -1, -1, "pm100"),    # k = 1: constant hash, t = 15
     (31, 1, 5, 4096, 4, 0, -1, -1, "pm100"),
-    (31, 1, 5, 1024, 4, 1, 2, -1, "pm100"),
+    (31, 1, 5, 1024, 4, 1, 3, -1, "pm100"),
+    (31, 1, 5, 1 << 16, 4, 0, 2, -1, "pm100"),
     (31, 1, 3, 32, 3, 0, 1, -1, "unit"),
     (89, 1, 5, 4096, 4, 0, -1, -1, "pm100"),
     (89, 1, 5, 1024, 4, 1, 1, -1, "unit"),
-    (89, 1, 3, 16, 5, 0, 2, -1, "pm100"),
+    (89, 1, 3, 16, 5, 0, 3, -1, "pm100"),
+    (89, 1, 5, 1 << 15, 4, 1, 2, -1, "pm100"),
     (64, 59, 5, 4096, 4, 0, -1, -1, "pm100"),
     (64, 59, 7, 1024, 4, 1, 1, -1, "unit"),
-    (64, 59, 1, 64, 2, 0, 2, -1, "pm100"),
+    (64, 59, 1, 64, 2, 0, 3, -1, "pm100"),
+    (64, 59, 7, 1 << 16, 4, 0, 2, -1, "unit"),
 ]
 
 
@@ -190,7 +197,8 @@ def test_cs_update_parity(env, case):
     seed = 1000 + t * 31 + k
     sk, C, f2, rows = run_sketch(torch, ms, b, c, t, m, k, mode, keys, w, seed, place, strategy)
     ll = sk.last_launch()
-    if place >= 0 and ll["place"] != place:
+    small = t * m * 4 <= 112 * 1024  # small sketches own no replicas: place 2 runs as 3
+    if place >= 0 and ll["place"] != place and not (place == 2 and small and ll["place"] == 3):
         pytest.fail("launch fell back from place %d to %s" % (place, ll))
     check_sketch(sk, C, f2, rows, b, c, k, mode, keys, w, seed)
 
@@ -226,10 +234,15 @@ def test_extreme_weights_take_exact_path(env):
     keys = make_keys(61, 1, n, 41)
     w = datagen.i32_range(42, -2 ** 31, 2 ** 31 - 1, n)
     w[:6] = [-2 ** 31, 2 ** 31 - 1, -2 ** 31, -2 ** 31, 2 ** 31 - 1, 0]
-    for place in (0, 1, 2):
+    for place in (0, 1, 2, 3):
         sk, C, f2, rows = run_sketch(torch, ms, 61, 1, t, m, 4, 0, keys, w, 3, place=place,
                                      strategy=1, blocks=4)
         check_sketch(sk, C, f2, rows, 61, 1, 4, 0, keys, w, 3)
+    # a sketch with replicas: int32 replica counters must not overflow either
+    sk, C, f2, rows = run_sketch(torch, ms, 61, 1, 5, 1 << 15, 4, 0, keys, w, 3, place=2,
+                                 strategy=1, blocks=16)
+    assert sk.last_launch()["place"] == 2
+    check_sketch(sk, C, f2, rows, 61, 1, 4, 0, keys, w, 3)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 5, 7, 1023, 1024, 1025])
@@ -321,3 +334,30 @@ def test_many_sketches_same_stream_differ_only_by_seed(env):
         sk.update(dk)
         vals.add(sk.f2())
     assert len(vals) > 1
+
+
+@pytest.mark.parametrize("place,replicas,aggregate", [(2, 1, 1), (2, 4, 0), (2, 32, 1), (3, 0, 1),
+                                                      (2, 16, 1)])
+@pytest.mark.parametrize("b,c", [(61, 1), (31, 1), (89, 1)])
+def test_global_replicas_and_warp_aggregation(env, place, replicas, aggregate, b, c):
+    """Zipf keys (many equal keys per warp), unit weights, a sketch too large for
+    shared memory: global replicas and warp aggregation must stay exact."""
+    torch, ms = env
+    n, t, m, k, seed = 100003, 7, 1 << 15, 4, 31
+    z = datagen.zipf(5, 1.1, 1 << 20, n)
+    if b == 31:
+        keys = (z & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    elif b == 89:
+        keys = np.stack([z, z ^ np.uint64(0x5555)], axis=1).astype(np.uint64)
+    else:
+        keys = z
+    sk = ms.Sketch(t=t, m=m, k=k, b=b, c=c, seed=seed)
+    sk.set_launch(place=place, replicas=replicas, aggregate=aggregate)
+    sk.update(to_dev(torch, keys))
+    ll = sk.last_launch()
+    assert ll["place"] == place and (place == 3 or ll["replicas"] == replicas), ll
+    C = sk.counters().cpu().numpy()
+    coeffs = oracle.sketch_coeffs(b, c, k, t, 0, seed)
+    want = oracle.cs_update(b, c, k, t, m, 0, coeffs, keys)
+    assert np.array_equal(C, want)
+    assert sk.f2() == oracle.f2_estimate(want)
