@@ -194,6 +194,30 @@ ms_status cs_update(cs_sketch* sk, const void* keys_dev, const int32_t* weights_
 ms_status cs_estimate_f2(const cs_sketch* sk, ms_u128* out_dev, ms_u128* rows_dev, void* stream);
 
 /*
+ * cs_estimate_f2_noalloc -- the same F2 estimate (and optional row values) as
+ * cs_estimate_f2, computed from a caller's counter array, and allocating
+ * nothing.  The paper has no counterpart: this is for callers that cannot
+ * call cudaMalloc, such as a serving loop that must not allocate once it is
+ * running (a device allocation can block and synchronize the whole device) or
+ * code that works inside a memory budget that is already spent.
+ *  counters_dev: t*m int64 counters, row-major (for a sketch: cs_counters).
+ *  out_dev, rows_dev: as in cs_estimate_f2 (rows_dev may be NULL).
+ *  t odd, m a power of two >= 2; t > 15 or m > 2^24 is beyond the scratch
+ *  array and returns MS_ERR_OUT_OF_RANGE.
+ *  Scratch: one file-scope device array of 15,616 bytes (up to 960 partial
+ *  sums and a ticket), which every GPU that loads the library holds until the
+ *  process exits.  The first call on a device looks up that array's device
+ *  address (once per device, with that device current); make that first call
+ *  before any stream capture begins.  Each call first clears the ticket on
+ *  `stream`.  All calls share the one array, so calls that overlap on the GPU
+ *  (for example on two streams) race and give wrong results: keep them ordered
+ *  on one stream.
+ *  Errors: INVALID_ARG, OUT_OF_RANGE, MISALIGNED, CUDA.
+ */
+ms_status cs_estimate_f2_noalloc(const int64_t* counters_dev, int t, uint32_t m, ms_u128* out_dev,
+                                 ms_u128* rows_dev, void* stream);
+
+/*
  * cs_point_query -- the estimate of f_x for each key: median over rows r of
  * sign_r(x) * C[r][bucket_r(x)] (the point-query use of the Count Sketch,
  * Sec. 1.4).  out_dev: n int64.  Errors: INVALID_ARG, CUDA.
