@@ -272,9 +272,10 @@ def run_ours(args, wl):
         e2e_s = float(tt.item())
     assert ms.u128_to_int(f2_h) == f2_est
 
-    # integer-multiply peak on this GPU (the roofline's denominator)
-    imad_rate, _ = ms.probe_mul128(variant=1, iters=1 << 14)
+    # integer-multiply peaks on this GPU: 64x64->128 products (the roofline's
+    # denominator) and 32x32->64 multiply-adds (context)
     mul_rate, _ = ms.probe_mul128(variant=0, iters=1 << 12)
+    imad_rate, _ = ms.probe_mul128(variant=1, iters=1 << 13)
 
     if rank != 0:
         if world > 1:
@@ -285,7 +286,7 @@ def run_ours(args, wl):
     kern_avg_s = statistics.mean(kern_ms) * 1e-3
     mul128_per_key = t * 3 * (2 if mode == 1 else 1)
     achieved_mul = n * mul128_per_key / kern_avg_s
-    peak_mul = imad_rate / 4.0  # 4 32x32->64 partial products per 64x64 product
+    peak_mul = mul_rate
     bytes_per_key = 8 + (4 if w is not None else 0)
     hbm_peak = 6787.9
     try:
@@ -321,9 +322,10 @@ def run_ours(args, wl):
             "kernel": "k_cs_update",
             "kernel_ms": statistics.mean(kern_ms),
             "mul128_per_key": mul128_per_key,
-            "peak_source": "ms_probe_mul128 variant 1 (independent 32x32->64 multiply-adds on "
-                           "every SM, measured in this run) / 4 partial products per 64x64 product",
-            "probe_mul64x64_per_s": mul_rate,
+            "peak_source": "ms_probe_mul128 variant 0: independent 64x64->128 products "
+                           "(low half by multiplication, high half by __umul64hi), 8 chains per "
+                           "thread on every SM, measured in this run",
+            "probe_mad_wide_32x32_per_s": imad_rate,
             "hbm": {"achieved_gbs": n * bytes_per_key / kern_avg_s / 1e9, "peak_gbs": hbm_peak,
                     "frac": n * bytes_per_key / kern_avg_s / 1e9 / hbm_peak},
         },

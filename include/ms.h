@@ -282,15 +282,18 @@ ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* th
 /* ---------------------------------------------------- integer-pipe peak probe */
 
 /*
- * ms_probe_mul128 -- measures this GPU's throughput of independent 64x64->128
- * bit products (the unit the hashing roofline is counted in) with a kernel
- * that runs `iters` independent product chains per thread on every SM.
- * Writes products/s to *rate and the kernel time in ms to *ms.  `sink_dev`
- * (8 bytes) receives a checksum so the work cannot be elided.  Synchronous.
- *  variant 0: full 64x64->128 product (low 64 bits and __umul64hi).
- *  variant 1: one 32x32->64 multiply-add (the partial product it is built of).
+ * ms_probe_mul128 -- measures this GPU's throughput of independent integer
+ * multiplies with a kernel that runs 8 independent chains of `iters` steps per
+ * thread on every SM.  Writes operations/s to *rate and the kernel time in ms
+ * to *ms.  `sink_dev` (8 bytes) receives a checksum so the work cannot be
+ * elided.  Synchronous.
+ *  variant 0: one full 64x64->128 product per step (low 64 bits by
+ *             multiplication, high 64 bits by __umul64hi) -- the unit the
+ *             hashing roofline is counted in.
+ *  variant 1: one 32x32->64 multiply-add (mad.wide.u32), the partial product
+ *             the limb arithmetic is built of.
  *  variant 2: one 32-bit multiply-add (low word only).
- *  variant 3: one 32-bit three-input integer add (the integer ALU pipe).
+ *  variant 3: one 32-bit integer add.
  */
 ms_status ms_probe_mul128(int variant, int iters, uint64_t* sink_dev, double* rate, double* ms);
 

@@ -399,19 +399,27 @@ cudaError_t launch_divmod(int prime, const ms_u128* v, ms_u128* q, void* r, u64 
 
 // ================================================================ probe
 //
-// Throughput of independent multiplies on every SM.  Each thread runs 8
-// independent chains so that latency is hidden; the chains' final values are
+// Throughput of independent integer multiplies on every SM.  Each thread runs
+// 8 independent chains so that latency is hidden; the chains' final values are
 // folded into one checksum so nothing can be removed.
-//  variant 0: a <- lo(a*b) ^ hi(a*b), a full 64x64->128 product per step
-//  variant 1: a <- lo32(a) * b32 + a, one 32x32->64 multiply-add per step
-//  variant 2: x <- x * b32 + c, one 32-bit multiply-add (low word) per step
-//  variant 3: x <- x + b32 + y, one 32-bit three-input add per step
+//  variant 0: a <- lo64(a*b) ^ hi64(a*b): one full 64x64->128 product (low half
+//             by multiplication, high half by __umul64hi) per step
+//  variant 1: w <- x*b + w (mad.wide.u32): one 32x32->64 multiply-add per step,
+//             chained only through the 64-bit addend
+//  variant 2: x <- y*b + x (mad.lo.u32): one 32-bit multiply-add per step
+//  variant 3: x <- x + y (add.u32): one 32-bit add per step
 __global__ void __launch_bounds__(256) k_probe(int variant, int iters, u64 seed, u64* sink) {
-    u64 a[8];
+    u64 a[8], wv[8];
+    u32 x[8], y[8];
     const u64 b = seed | 1ull;
     const u32 b32 = (u32)(seed >> 7) | 1u;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) a[c] = seed * (threadIdx.x + 1 + c) + blockIdx.x;
+    for (int c = 0; c < 8; ++c) {
+        a[c] = seed * (threadIdx.x + 1 + c) + blockIdx.x;
+        x[c] = (u32)a[c];
+        y[c] = (u32)(a[c] >> 29) ^ (u32)c;
+        wv[c] = a[c] ^ 0x5555ull;
+    }
     if (variant == 0) {
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
@@ -420,32 +428,24 @@ __global__ void __launch_bounds__(256) k_probe(int variant, int iters, u64 seed,
     } else if (variant == 1) {
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) a[c] = (u64)(u32)a[c] * b32 + a[c];
+            for (int c = 0; c < 8; ++c)
+                asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(wv[c]) : "r"(x[c]), "r"(b32));
         }
-    } else if (variant == 2) {  // 32-bit multiply-add (low word only)
-        u32 x[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) x[c] = (u32)a[c];
+    } else if (variant == 2) {
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) x[c] = x[c] * b32 + (u32)c;
+            for (int c = 0; c < 8; ++c)
+                asm volatile("mad.lo.u32 %0, %1, %2, %0;" : "+r"(x[c]) : "r"(y[c]), "r"(b32));
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) a[c] = x[c];
-    } else {  // variant 3: 32-bit three-input add (integer ALU)
-        u32 x[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) x[c] = (u32)a[c];
+    } else {
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) x[c] = x[c] + b32 + x[(c + 1) & 7];
+            for (int c = 0; c < 8; ++c) asm volatile("add.u32 %0, %0, %1;" : "+r"(x[c]) : "r"(y[c]));
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) a[c] = x[c];
     }
     u64 s = 0;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) s ^= a[c];
+    for (int c = 0; c < 8; ++c) s ^= a[c] ^ wv[c] ^ x[c];
     if (s == 0x1234567ull) *sink = s;  // practically never taken; keeps the work live
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicXor(sink, s);
 }

@@ -284,8 +284,10 @@ __device__ __forceinline__ void apply_update(int* tile, u32 tile_saddr, long lon
 
 // T, K > 0: compile-time rows and degree with ParamCoef; T = K = 0: runtime t
 // and k with coefficients staged from coef_dev into shared memory.
+// Two-for-one kernels are capped at 64 registers (two 512-thread blocks per SM);
+// two-polynomial kernels keep twice the key state live and get 128.
 template <class F, int T, int K, int MODE, int PLACE, int STRAT>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, (MODE == CS_TWO_POLY) ? 1 : 2)
 k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1) * T, K> pc) {
     typedef FieldOps<F> Ops;
     typedef typename Ops::val_t val_t;
@@ -378,21 +380,18 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                 for (int q = 0; q < 4; ++q) {
                     const u32 al[3] = {pc.lo[fb * 4 + 1], pc.lo[fb * 4 + 2], pc.lo[fb * 4 + 3]};
                     const u32 ah[3] = {pc.hi[fb * 4 + 1], pc.hi[fb * 4 + 2], pc.hi[fb * 4 + 3]};
-                    const u64 h = msf::P61::power_sum<3>(xp[q], pc.w[fb * 4], al, ah);
-                    u32 sb;
+                    u32 bucket, sb;
+                    msf::P61::power_sum_bs(xp[q], pc.w[fb * 4], al, ah, mask, bucket, sb);
                     if (MODE == CS_TWO_POLY) {
                         const int fs = fb + 1;
                         const u32 sl[3] = {pc.lo[fs * 4 + 1], pc.lo[fs * 4 + 2], pc.lo[fs * 4 + 3]};
                         const u32 sh[3] = {pc.hi[fs * 4 + 1], pc.hi[fs * 4 + 2], pc.hi[fs * 4 + 3]};
-                        const u64 g = msf::P61::power_sum<3>(xp[q], pc.w[fs * 4], sl, sh);
-                        sb = msf::P61::sign_bit(g);
-                    } else {
-                        sb = msf::P61::sign_bit(h);
+                        u32 unused;
+                        msf::P61::power_sum_bs(xp[q], pc.w[fs * 4], sl, sh, mask, unused, sb);
                     }
                     if (wt[q] != 0)
-                        apply_update<PLACE>(tile, tile_saddr, a.counters, r,
-                                            msf::P61::bucket(h, mask), sb, wt[q], big[q], m, log2m,
-                                            lcs);
+                        apply_update<PLACE>(tile, tile_saddr, a.counters, r, bucket, sb, wt[q],
+                                            big[q], m, log2m, lcs);
                 }
             }
         } else {

@@ -113,6 +113,41 @@ struct P61 {
 
     __device__ static __forceinline__ u32 bucket(u64 h, u32 mask) { return (u32)h & mask; }
     __device__ static __forceinline__ u32 sign_bit(u64 h) { return (u32)(h >> 60) & 1u; }
+
+    // 32x32 -> 64-bit multiply-add, a * b + c (one wide integer multiply-add).
+    __device__ static __forceinline__ u64 madw(u32 a, u32 b, u64 c) {
+        u64 d;
+        asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+        return d;
+    }
+
+    // Bucket and sign bit of the canonical residue of a lazily reduced
+    // y < 2^61 + 8.  Only y in [p, 2^61 + 8) -- at most 9 of those values --
+    // needs the subtraction, and then y.hi >= 0x1FFFFFFF; every other value
+    // takes the short path.
+    __device__ static __forceinline__ void bucket_sign(u64 y, u32 mask, u32& bucket, u32& sign) {
+        if ((u32)(y >> 32) >= 0x1FFFFFFFu) y = canon(y);
+        bucket = (u32)y & mask;
+        sign = (u32)(y >> 60) & 1u;
+    }
+
+    // power_sum<3> returning the bucket and sign bit of the canonical value:
+    // the same accumulators with explicit wide multiply-adds, then the same
+    // two folds (bounds as in power_sum).
+    __device__ static __forceinline__ void power_sum_bs(const Split* xp, u64 a0, const u32* al,
+                                                        const u32* ah, u32 mask, u32& bucket,
+                                                        u32& sign) {
+        u64 A = a0, H = 0, M = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            A = madw(al[i], xp[i].lo, A);
+            H = madw(ah[i], xp[i].hi2, H);
+            M = madw(ah[i], xp[i].lo, M);
+            M = madw(al[i], xp[i].hi, M);
+        }
+        const u64 S = fold(A) + H + (M >> 30) + ((M & 0x3FFFFFFFull) << 31);
+        bucket_sign(fold(S), mask, bucket, sign);
+    }
 };
 
 // ---------------------------------------------------------------- p = 2^31-1

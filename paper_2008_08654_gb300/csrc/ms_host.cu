@@ -547,11 +547,13 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::Update
         e = msk::query_cs_update_occupancy(sk->prime, a, sk->words.data(), cfg, &occ);
         if (e != cudaSuccess || occ < 1) return cuda_fail(e, "occupancy");
     }
+    // Two waves of resident blocks: the second wave fills the gaps the first
+    // leaves as its blocks finish at different times.
     long long capacity;
     if (cfg.place == msk::PLACE_DSMEM)
         capacity = (long long)occ * cfg.cluster;  // occ = co-resident clusters
     else
-        capacity = (long long)occ * d.sms * (ov.blocks_per_sm > 0 ? 1 : 1);
+        capacity = 2ll * occ * d.sms;
     if (ov.blocks_per_sm > 0 && cfg.place != msk::PLACE_DSMEM) {
         long long want = (long long)ov.blocks_per_sm * d.sms;
         if (want < capacity) capacity = want;
