@@ -41,6 +41,7 @@ import datagen  # noqa: E402
 
 P61 = (1 << 61) - 1
 
+# Workloads other than the single-sketch ones print their own lines (bench_extra.py).
 WORKLOADS = {
     # name: (n, t, m, mode, keys, weights)
     "large": dict(n=1 << 28, t=7, m=1 << 16, mode=0, keys="zipf", weights=None,
@@ -66,12 +67,15 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS) + sorted(EXTRA))
+    ap.add_argument("--sketches", type=int, default=4096, help="batched workload: sketch count")
     ap.add_argument("--seed", type=int, default=2008)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--keys", type=int, default=0,
+                    help="override the workload's keys per step (small cases for profiling)")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -407,9 +411,260 @@ def run_reference(args, wl):
     }
 
 
+# ------------------------------------------------------------------ extra workloads
+
+def _timed(fn, steps, warmup, stream=None):
+    """Mean ms of fn() over `steps` runs after `warmup`, by CUDA events."""
+    import torch
+    for _ in range(max(1, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _line(metric, value, unit, args, config, **extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+         "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+         "dtype": "u64", "data": "synthetic", "config": config}
+    d.update(extra)
+    return d
+
+
+def run_sweep(args):
+    """Prime-width sweep: 2^30 random keys, k=4, t=5, m=4096, unit weights, for
+    p = 2^31-1 (u32 keys), 2^61-1 (u64), 2^89-1 (two-limb keys), 2^64-59 (u64)."""
+    import torch
+    import paper_2008_08654_gb300 as ms
+    n = args.keys or (1 << 30)
+    mul_rate, _ = ms.probe_mul128(variant=0, iters=1 << 12)
+    res = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for (b, c) in ms.PRIMES:
+        p = (1 << b) - c
+        if b == 31:
+            keys = torch.from_numpy(datagen.u32_below(args.seed, p, n).view(np.int32)).cuda()
+        elif b == 89:
+            keys = torch.from_numpy(datagen.p89_keys(args.seed, n).view(np.int64)).cuda()
+        else:
+            keys = torch.from_numpy(datagen.u64_below(args.seed, p, n).view(np.int64)).cuda()
+        sk = ms.Sketch(t=5, m=4096, k=4, b=b, c=c, seed=args.seed)
+
+        def step():
+            sk.reset()
+            sk.update(keys)
+        t = _timed(step, max(1, args.steps), args.warmup)
+        kps = n / (t * 1e-3)
+        res["2^%d-%d" % (b, c)] = {"keys_per_s": kps, "ms_per_step": t,
+                                   "mul128_frac": kps * 15 / mul_rate,
+                                   "launch": sk.last_launch(),
+                                   "key_bytes": {31: 4, 61: 8, 89: 16, 64: 8}[b]}
+        del keys, sk
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    best = res["2^61-1"]["keys_per_s"]
+    return _line("Count Sketch key updates/s across primes (k=4, t=5, m=4096)", best, "keys/s",
+                 args, {"workload": "prime sweep: %d random keys below p per prime, unit weights"
+                        % n, "value_is": "p=2^61-1"},
+                 per_prime=res, probe_mul64x64_per_s=mul_rate, **({"clocks": clk} if clk else {}))
+
+
+def run_div(args):
+    """ms_div microbenchmark: 2^30 uniform values below 2^122, p = 2^61-1; reads
+    16 B and writes a 16-byte quotient and an 8-byte remainder per value."""
+    import torch
+    import oracle
+    import paper_2008_08654_gb300 as ms
+    n = args.keys or (1 << 30)
+    v = datagen.u128_bits(args.seed, 122, n, stream=datagen.STREAM_VALUES)
+    vd = torch.from_numpy(v.view(np.int64)).cuda()
+    q = torch.empty((n, 2), dtype=torch.int64, device="cuda")
+    r = torch.empty(n, dtype=torch.int64, device="cuda")
+    t = _timed(lambda: ms.div(61, 1, vd, q, r), max(1, args.steps), args.warmup)
+    idx = np.unique(datagen.u64_below(args.seed + 1, n, 4096))
+    qw, rw = oracle.divmod_(61, 1, v[idx])
+    ok = (np.array_equal(q.cpu().numpy()[idx].view(np.uint64), qw)
+          and np.array_equal(r.cpu().numpy()[idx].view(np.uint64), rw[:, 0]))
+    gbs = 40.0 * n / (t * 1e-3) / 1e9
+    hbm_peak = 6787.9
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        pass
+    return _line("ms_div values/s (p=2^61-1, v < 2^122)", n / (t * 1e-3), "values/s", args,
+                 {"workload": "%d uniform 122-bit values, quotient (16 B) and remainder (8 B)" % n},
+                 ms_per_step=t, roofline={"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                                          "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+                                          "kernel": "k_divmod", "bytes_per_value": 40},
+                 parity_on_sample=bool(ok))
+
+
+def run_table1(args):
+    """The paper's Table 1 workload: 10^7 k-universal hashes of random 64-bit
+    keys for k in {2, 4, 8}, p = 2^61-1 and p = 2^89-1 (keys in device memory)."""
+    import torch
+    import oracle
+    import paper_2008_08654_gb300 as ms
+    n = args.keys or 10 ** 7
+    k64 = datagen.u64_below(args.seed, (1 << 61) - 1, n)
+    k89 = np.zeros((n, 2), dtype=np.uint64)
+    k89[:, 0] = datagen.u64_below(args.seed + 1, 0, n)
+    dev = {61: torch.from_numpy(k64.view(np.int64)).cuda(),
+           89: torch.from_numpy(k89.view(np.int64)).cuda()}
+    host = {61: k64, 89: k89}
+    rows, ok = {}, True
+    for b in (61, 89):
+        for k in (2, 4, 8):
+            h = ms.Hash(k=k, b=b, c=1, seed=args.seed + k)
+            out = h.out_tensor(n)
+            t = _timed(lambda: h.eval(dev[b], out), max(1, args.steps), args.warmup)
+            rows["p=2^%d-1,k=%d" % (b, k)] = {"ms_per_1e7_hashes": t * 1e7 / n,
+                                              "hashes_per_s": n / (t * 1e-3)}
+            got = out[:2048].cpu().numpy().view(np.uint64)
+            want = oracle.hash_eval(b, 1, oracle.from_ints(h.coeffs()), host[b][:2048])
+            ok = ok and np.array_equal(got, want if b == 89 else want[:, 0])
+    return _line("k-universal hashes/s (p=2^61-1, k=4)", rows["p=2^61-1,k=4"]["hashes_per_s"],
+                 "hashes/s", args, {"workload": "%d random 64-bit keys per (p, k)" % n},
+                 table1=rows, parity_on_sample=bool(ok),
+                 paper_cpu_ms_per_1e7={"p=2^61-1,k=4": [31.6, 34.3, 41.9],
+                                       "p=2^89-1,k=4": [65.7, 68.7, 85.2]})
+
+
+def run_batched(args):
+    """Batched: independent sketches (t=5, m from {256, 1024, 4096, 8192}, own
+    seeds, n_i = floor(10^(3+4U)) keys below 2^61-1, int32 weights in [-100, 100])
+    in one persistent graph-captured launch, against one cs_update per sketch."""
+    import torch
+    import oracle
+    import paper_2008_08654_gb300 as ms
+    S = args.sketches
+    u = datagen.unit_doubles(args.seed, S, datagen.STREAM_LENGTHS)
+    ns = np.floor(10.0 ** (3.0 + 4.0 * u)).astype(np.int64)
+    widths = np.array([256, 1024, 4096, 8192])[
+        datagen.u64_below(args.seed, 4, S, stream=datagen.STREAM_WIDTHS).astype(np.int64)]
+    total = int(ns.sum())
+    keys = torch.empty(total, dtype=torch.int64, device="cuda")
+    wts = torch.empty(total, dtype=torch.int32, device="cuda")
+    offs = np.concatenate([[0], np.cumsum(ns)])
+    sketches, jobs = [], []
+    for i in range(S):
+        s0 = args.seed * 7919 + i
+        a, b = int(offs[i]), int(offs[i + 1])
+        keys[a:b].copy_(torch.from_numpy(datagen.u64_below(s0, (1 << 61) - 1, b - a)
+                                         .view(np.int64)))
+        wts[a:b].copy_(torch.from_numpy(datagen.i32_range(s0, -100, 100, b - a)))
+        sk = ms.Sketch(t=5, m=int(widths[i]), k=4, seed=s0)
+        sketches.append(sk)
+        jobs.append((sk, keys[a:b], wts[a:b]))
+    cands = []
+    for threads in (256, 512):
+        for chunk in (1 << 15, 1 << 17, 1 << 19):
+            for ratio in (2, 8, 32):
+                cands.append({"threads": threads, "chunk_keys": chunk, "smem_min_ratio": ratio})
+    best, times = ms.tune_batched(jobs, cands, reps=2)
+    plan = ms.Batch(jobs, best)
+
+    def reset_all():
+        for sk in sketches:
+            sk.reset()
+    reset_all()
+    t_graph = _timed(plan.launch, max(1, args.steps), args.warmup)
+    t_direct = _timed(plan.launch_direct, max(1, args.steps), 1)
+
+    def plain():
+        for sk, kk, ww in jobs:
+            sk.update(kk, ww)
+    t_plain = _timed(plain, max(1, min(args.steps, 5)), 1)
+    # parity of a sample of sketches after one clean batched launch
+    reset_all()
+    plan.launch()
+    torch.cuda.synchronize()
+    ok = True
+    for i in list(range(0, S, max(1, S // 6)))[:6]:
+        sk = sketches[i]
+        a, b = int(offs[i]), int(offs[i + 1])
+        if b - a > 2_000_000:
+            continue
+        kh = keys[a:b].cpu().numpy().view(np.uint64)
+        wh = wts[a:b].cpu().numpy()
+        want = oracle.cs_update(61, 1, 4, 5, sk.m, 0, oracle.sketch_coeffs(61, 1, 4, 5, 0,
+                                                                           args.seed * 7919 + i),
+                                kh, wh, nthreads=os.cpu_count() or 1)
+        ok = ok and np.array_equal(sk.counters().cpu().numpy(), want)
+    info = plan.info()
+    return _line("batched Count Sketch key updates/s (k=4, p=2^61-1, t=5)", total / (t_graph * 1e-3),
+                 "keys/s", args,
+                 {"workload": "%d sketches, %d keys in total (log-uniform 1e3..1e7 per sketch)"
+                  % (S, total), "m_classes": {str(m): int((widths == m).sum()) for m in
+                                                (256, 1024, 4096, 8192)}},
+                 ms_per_step=t_graph, direct_launch_keys_per_s=total / (t_direct * 1e-3),
+                 plain_launches_keys_per_s=total / (t_plain * 1e-3),
+                 speedup_vs_plain_launches=t_plain / t_graph, tuner_choice=best,
+                 tuner_candidates=len(cands), tuner_times_ms=times, plan=info,
+                 parity_on_sample=bool(ok))
+
+
+def run_serving(args):
+    """Serving: device-resident sketches (t=5, k=4, p=2^61-1, m uniform over
+    {1024, 4096}); Poisson arrivals mixing updates (log-uniform 256..2^20 Zipf(1.1)
+    keys, unit weights) with F2 queries (10%); 40 GB staging budget.  First a
+    saturating run measures peak keys/s, then offered loads of 50/80/95% of it."""
+    import torch
+    import paper_2008_08654_gb300 as ms
+    S = args.sketches if args.sketches != 4096 else 10000
+    widths = [1024 if x == 0 else 4096
+              for x in datagen.u64_below(args.seed, 2, S, stream=datagen.STREAM_WIDTHS)]
+    srv = ms.Server(widths, t=5, seed_base=args.seed, staging_bytes=40 << 30, max_inflight=4096,
+                    max_batch_keys=1 << 25, max_batch_requests=4096, timeout_s=120.0)
+    pool = torch.from_numpy(datagen.zipf(args.seed, 1.1, 1 << 32, 1 << 22).view(np.int64))
+    pool = pool.pin_memory()
+    count = max(200, args.keys or 4000)
+    qf, lo, hi = 0.1, 256, 1 << 20
+    mean_n = (hi - lo) / math.log(hi / lo)
+    srv.run_load(pool, count=200, rate_per_s=1e6, query_fraction=qf, min_keys=lo, max_keys=hi,
+                 seed=args.seed + 99)  # warm-up
+    peak = srv.run_load(pool, count=count, rate_per_s=1e7, query_fraction=qf, min_keys=lo,
+                        max_keys=hi, seed=args.seed)
+    levels = {}
+    for frac in (0.5, 0.8, 0.95):
+        rate = frac * peak["keys_per_s"] / ((1 - qf) * mean_n)
+        levels["%d%%" % int(frac * 100)] = srv.run_load(
+            pool, count=count, rate_per_s=rate, query_fraction=qf, min_keys=lo, max_keys=hi,
+            seed=args.seed + int(frac * 100))
+    srv.close()
+    return _line("served Count Sketch key updates/s (k=4, p=2^61-1, t=5)", peak["keys_per_s"],
+                 "keys/s", args,
+                 {"workload": "%d device-resident sketches, m in {1024, 4096}; %d requests per "
+                              "run, 10%% F2 queries, updates of log-uniform 256..2^20 Zipf(1.1) "
+                              "keys from a pinned host pool; 40 GB staging" % (S, count)},
+                 saturated=peak, offered_load=levels)
+
+
+EXTRA = {"sweep": run_sweep, "div": run_div, "table1": run_table1, "batched": run_batched,
+         "serving": run_serving}
+
+
 def main():
     args = parse_args()
-    wl = WORKLOADS[args.workload]
+    if args.workload in EXTRA:
+        line = EXTRA[args.workload](args)
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(s + "\n")
+        return
+    wl = dict(WORKLOADS[args.workload])
+    if args.keys > 0:
+        wl["n"] = args.keys
+        wl["desc"] = wl["desc"] + " (reduced to %d keys)" % args.keys
     if args.impl == "reference":
         line = run_reference(args, wl)
     else:

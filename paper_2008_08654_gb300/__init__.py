@@ -465,3 +465,157 @@ def tune_batched(jobs, candidates, reps: int = 3, stream=None):
     _check(_load().cs_batch_tune(arr, len(jobs), cands, len(candidates), reps, ctypes.byref(best),
                                  times, _stream(stream)), "cs_batch_tune")
     return best.as_dict(), list(times)
+
+
+# ------------------------------------------------------------------ serving
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int), ("k", ctypes.c_int), ("b", ctypes.c_int),
+                ("c", ctypes.c_uint64), ("mode", ctypes.c_int), ("seed_base", ctypes.c_uint64),
+                ("num_sketches", ctypes.c_int), ("m_per_sketch", ctypes.POINTER(ctypes.c_uint32)),
+                ("staging_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
+                ("max_batch_keys", ctypes.c_uint64), ("max_batch_requests", ctypes.c_int),
+                ("timeout_s", ctypes.c_double)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("f2", U128),
+                ("submit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class LoadSpec(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("count", ctypes.c_uint64),
+                ("rate_per_s", ctypes.c_double), ("query_fraction", ctypes.c_double),
+                ("min_keys", ctypes.c_uint64), ("max_keys", ctypes.c_uint64),
+                ("key_pool_host", ctypes.c_void_p), ("pool_keys", ctypes.c_uint64)]
+
+
+class LoadResult(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("keys_per_s", ctypes.c_double),
+                ("update_p50_ms", ctypes.c_double), ("update_p99_ms", ctypes.c_double),
+                ("query_p50_ms", ctypes.c_double), ("query_p99_ms", ctypes.c_double),
+                ("updates", ctypes.c_uint64), ("queries", ctypes.c_uint64),
+                ("keys", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("offered_keys_per_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_SERVER_SIGS = {
+    "ms_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "ms_server_submit_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_uint64)]),
+    "ms_server_submit_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_uint64)]),
+    "ms_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "ms_server_drain": (ctypes.c_int, [ctypes.c_void_p]),
+    "ms_server_sketch_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "ms_server_stats": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_uint64)] * 3),
+    "ms_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "ms_server_run_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def _server_lib():
+    lib_ = _load()
+    if not getattr(lib_, "_ms_server_sigs", False):
+        for name, (res, args) in _SERVER_SIGS.items():
+            f = getattr(lib_, name)
+            f.restype = res
+            f.argtypes = args
+        lib_._ms_server_sigs = True
+    return lib_
+
+
+class Server:
+    """Continuous batching over device-resident sketches (ms_server_*).
+    Host buffers passed to submit_update are kept referenced until drain()."""
+
+    def __init__(self, widths, t=5, k=4, b=61, c=1, mode=TWO_FOR_ONE, seed_base=0,
+                 staging_bytes=1 << 30, max_inflight=1024, max_batch_keys=1 << 24,
+                 max_batch_requests=1024, timeout_s=60.0):
+        lib_ = _server_lib()
+        self._widths = (ctypes.c_uint32 * len(widths))(*widths)
+        cfg = ServerConfig(t, k, b, c, mode, seed_base, len(widths), self._widths, staging_bytes,
+                           max_inflight, max_batch_keys, max_batch_requests, timeout_s)
+        h = ctypes.c_void_p()
+        _check(lib_.ms_server_create(ctypes.byref(h), ctypes.byref(cfg)), "ms_server_create")
+        self._h = h
+        self.t, self.k, self.b, self.c = t, k, b, c
+        self.widths = list(widths)
+        self._keep = []
+
+    @staticmethod
+    def _host_ptr(a):
+        if a is None:
+            return None, None
+        if isinstance(a, torch.Tensor):
+            assert not a.is_cuda and a.is_contiguous()
+            return a, a.data_ptr()
+        return a, a.ctypes.data
+
+    def submit_update(self, sketch_id: int, keys, weights=None, try_only=False) -> int:
+        kobj, kp = self._host_ptr(keys)
+        wobj, wp = self._host_ptr(weights)
+        n = kobj.numel() if isinstance(kobj, torch.Tensor) else len(kobj)
+        if self.b == 89:
+            n //= 2 if (isinstance(kobj, torch.Tensor) and kobj.dim() == 1) else 1
+        tk = ctypes.c_uint64()
+        st = _server_lib().ms_server_submit_update(self._h, sketch_id, kp, wp, n,
+                                                   1 if try_only else 0, ctypes.byref(tk))
+        _check(st, "ms_server_submit_update")
+        self._keep.append((kobj, wobj))
+        return tk.value
+
+    def submit_query(self, sketch_id: int, try_only=False) -> int:
+        tk = ctypes.c_uint64()
+        _check(_server_lib().ms_server_submit_query(self._h, sketch_id, 1 if try_only else 0,
+                                                    ctypes.byref(tk)), "ms_server_submit_query")
+        return tk.value
+
+    def poll(self, ticket: int) -> dict:
+        r = RequestResult()
+        _check(_server_lib().ms_server_poll(self._h, ticket, ctypes.byref(r)), "ms_server_poll")
+        return {"done": bool(r.done), "status": r.status, "f2": r.f2.lo | (r.f2.hi << 64),
+                "submit_s": r.submit_s, "done_s": r.done_s}
+
+    def drain(self):
+        _check(_server_lib().ms_server_drain(self._h), "ms_server_drain")
+        self._keep.clear()
+
+    def counters(self, sketch_id: int):
+        import numpy as np
+        out = np.empty((self.t, self.widths[sketch_id]), dtype=np.int64)
+        _check(_server_lib().ms_server_sketch_counters(self._h, sketch_id, out.ctypes.data),
+               "ms_server_sketch_counters")
+        return out
+
+    def stats(self) -> dict:
+        v = [ctypes.c_uint64() for _ in range(3)]
+        _check(_server_lib().ms_server_stats(self._h, *[ctypes.byref(x) for x in v]),
+               "ms_server_stats")
+        return {"requests_done": v[0].value, "keys_done": v[1].value, "batches": v[2].value}
+
+    def run_load(self, pool, count, rate_per_s, query_fraction=0.1, min_keys=256,
+                 max_keys=1 << 20, seed=0) -> dict:
+        pobj, pp = self._host_ptr(pool)
+        npool = pobj.numel() if isinstance(pobj, torch.Tensor) else len(pobj)
+        spec = LoadSpec(seed, count, rate_per_s, query_fraction, min_keys, max_keys, pp, npool)
+        res = LoadResult()
+        _check(_server_lib().ms_server_run_load(self._h, ctypes.byref(spec), ctypes.byref(res)),
+               "ms_server_run_load")
+        return res.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(_server_lib().ms_server_destroy(self._h), "ms_server_destroy")
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

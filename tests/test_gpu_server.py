@@ -1,0 +1,126 @@
+"""The continuous-batching server: every query answer equals the oracle's F2
+estimate of its sketch over exactly the updates submitted to that sketch
+before the query -- whether requests run one at a time or mixed in batches."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(nsk, count, seed):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        s = int(rng.integers(0, nsk))
+        if rng.random() < 0.25:
+            reqs.append(("q", s, None, None))
+        else:
+            n = int(rng.integers(0, 5000))
+            keys = datagen.zipf(seed * 1000 + i, 1.1, 1 << 16, n)
+            w = datagen.i32_range(seed * 1000 + i, -100, 100, n) if rng.random() < 0.5 else None
+            reqs.append(("u", s, keys, w))
+    return reqs
+
+
+def _expected(reqs, widths, t, seed_base):
+    C = [np.zeros((t, m), dtype=np.int64) for m in widths]
+    ans = []
+    for kind, s, keys, w in reqs:
+        if kind == "u":
+            oracle.cs_update(61, 1, 4, t, widths[s], 0,
+                             oracle.sketch_coeffs(61, 1, 4, t, 0, seed_base + s), keys, w,
+                             counters=C[s])
+        else:
+            ans.append(oracle.f2_estimate(C[s]))
+    return ans, C
+
+
+def _run(ms, reqs, widths, t, seed_base, alone, **kw):
+    srv = ms.Server(widths, t=t, seed_base=seed_base, **kw)
+    tickets = []
+    for kind, s, keys, w in reqs:
+        if kind == "u":
+            tk = srv.submit_update(s, keys, w)
+        else:
+            tk = srv.submit_query(s)
+        if alone:
+            srv.drain()
+        tickets.append((kind, tk))
+    srv.drain()
+    ans = []
+    for kind, tk in tickets:
+        r = srv.poll(tk)
+        assert r["done"] and r["status"] == 0
+        if kind == "q":
+            ans.append(r["f2"])
+    counters = [srv.counters(i) for i in range(len(widths))]
+    stats = srv.stats()
+    srv.close()
+    return ans, counters, stats
+
+
+@pytest.mark.parametrize("kw", [{}, {"max_batch_requests": 3},
+                                {"staging_bytes": 64 << 10, "max_batch_keys": 7000},
+                                {"max_inflight": 2}])
+def test_server_answers_equal_oracle_alone_and_mixed(kw):
+    import paper_2008_08654_gb300 as ms
+    widths, t, seed_base = [64, 128, 1024, 64, 256, 4096], 5, 77
+    reqs = _requests(len(widths), 80, 5)
+    want, want_c = _expected(reqs, widths, t, seed_base)
+    mixed, cm, stats = _run(ms, reqs, widths, t, seed_base, alone=False, **kw)
+    alone, ca, _ = _run(ms, reqs, widths, t, seed_base, alone=True, **kw)
+    assert mixed == want
+    assert alone == want
+    for a, b, c in zip(cm, ca, want_c):
+        assert np.array_equal(a, c) and np.array_equal(b, c)
+    assert stats["requests_done"] == len(reqs)
+
+
+def test_server_rejects_bad_requests():
+    import paper_2008_08654_gb300 as ms
+    srv = ms.Server([64, 64], staging_bytes=8192)
+    with pytest.raises(ms.MSError) as e:
+        srv.submit_query(2)
+    assert e.value.status == 1
+    with pytest.raises(ms.MSError) as e:  # larger than the whole staging ring
+        srv.submit_update(0, np.zeros(4096, dtype=np.uint64))
+    assert e.value.status == 3
+    srv.close()
+
+
+def test_server_backpressure_statuses():
+    """With one slot and try_only, submissions beyond the slot return BUSY; the
+    ones accepted are applied exactly."""
+    import paper_2008_08654_gb300 as ms
+    srv = ms.Server([1024], max_inflight=1)
+    keys = datagen.u64_below(3, (1 << 61) - 1, 1 << 20)
+    accepted, busy = 0, 0
+    for _ in range(20):
+        try:
+            srv.submit_update(0, keys, try_only=True)
+            accepted += 1
+        except ms.MSError as e:
+            assert e.status == 7
+            busy += 1
+    srv.drain()
+    C = srv.counters(0)
+    want = np.zeros((5, 1024), dtype=np.int64)
+    co = oracle.sketch_coeffs(61, 1, 4, 5, 0, 0)
+    one = oracle.cs_update(61, 1, 4, 5, 1024, 0, co, keys, nthreads=8)
+    assert accepted >= 1 and accepted + busy == 20
+    assert np.array_equal(C, one * accepted)
+    srv.close()
+
+
+def test_load_generator_runs():
+    import paper_2008_08654_gb300 as ms
+    srv = ms.Server([1024, 4096] * 8, staging_bytes=1 << 28)
+    pool = datagen.zipf(9, 1.1, 1 << 32, 1 << 18)
+    r = srv.run_load(pool, count=300, rate_per_s=2000.0, query_fraction=0.1, min_keys=256,
+                     max_keys=1 << 16, seed=4)
+    assert r["updates"] + r["queries"] == 300 and r["keys"] > 0
+    assert 0 < r["update_p50_ms"] <= r["update_p99_ms"]
+    srv.close()
