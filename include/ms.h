@@ -265,9 +265,11 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  *  threads (multiple of 32, <= 512), blocks (total), blocks_per_sm (cap),
  *  cluster (power of two <= 16, place 1 only), replicas (power of two <= 32,
  *  place 2 only; capped at the replicas the sketch owns; default 32),
- *  aggregate (0/1, default 1: with unit weights and place 2 or 3, lanes of a
- *  warp holding the same key send one atomic carrying their count; every key
- *  is still hashed).
+ *  aggregate (0, 1 or 2, default 1; unit weights and place 2 or 3 only):
+ *  1 = lanes of a warp holding the same key send one atomic carrying their
+ *  count; 2 = also a per-block table of 4096 keys in shared memory (one-word
+ *  keys: every prime but 2^89-1) whose counts the block adds once per row at
+ *  its end.  Every key is still hashed; the counters are identical.
  * Errors: INVALID_ARG.
  */
 ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int threads, int blocks,

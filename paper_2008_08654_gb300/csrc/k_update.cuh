@@ -229,6 +229,43 @@ __device__ __forceinline__ u32 match_key(const u128x& k) {
     return __match_any_sync(0xffffffffu, k.lo) & __match_any_sync(0xffffffffu, k.hi);
 }
 
+// ------------------------------------------------------------ hot-key table
+//
+// A direct-mapped table in shared memory for one-word keys: slot i holds a key
+// (or EMPTY) and how many times this block saw it.  Used only for unit weights
+// with the global placement: a key that owns its slot (or claims an empty one)
+// adds 1 to the slot's count instead of t atomics to global memory; at the end
+// the block adds each slot's count once per row.  Every key is still hashed.
+constexpr u64 HOT_EMPTY = ~0ull;
+
+template <class K>
+struct HotKey {
+    static constexpr bool OK = false;
+};
+template <>
+struct HotKey<u64> {
+    static constexpr bool OK = true;
+};
+template <>
+struct HotKey<u32> {
+    static constexpr bool OK = true;
+};
+
+// Returns true when the group of w occurrences was counted in the table.
+// Keys equal to EMPTY never use it.
+__device__ __forceinline__ bool hot_add(u64* hkey, int* hcnt, int log2slots, u64 key, int w) {
+    if (key == HOT_EMPTY) return false;
+    const u32 slot = (u32)((key * 0x9E3779B97F4A7C15ull) >> (64 - log2slots));
+    u64 cur = hkey[slot];
+    if (cur == HOT_EMPTY) {
+        cur = atomicCAS((unsigned long long*)&hkey[slot], HOT_EMPTY, key);
+        if (cur == HOT_EMPTY) cur = key;  // claimed by this thread
+    }
+    if (cur != key) return false;
+    atomicAdd(&hcnt[slot], w);
+    return true;
+}
+
 // ------------------------------------------------------------ cluster helpers
 
 __device__ __forceinline__ u32 cluster_rank() {
@@ -312,6 +349,17 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                     : reinterpret_cast<int*>(smem);
     const u32 tile_cells = (PLACE == PLACE_GLOBAL) ? 0u : (u32)t * mloc;
     u64* scoef = reinterpret_cast<u64*>(smem + (size_t)tile_cells * 4u);
+    // PLACE_GLOBAL: hot-key table after the coefficients
+    const int hot_log2 = (PLACE == PLACE_GLOBAL && HotKey<typename Ops::key_t>::OK &&
+                          a.weights == nullptr) ? a.hot_log2 : 0;
+    const u32 hot_slots = hot_log2 ? (1u << hot_log2) : 0u;
+    u64* hkey = reinterpret_cast<u64*>(
+        smem + (((size_t)tile_cells * 4u + (GENERIC ? (size_t)t * NF * k * W * 8 : 0) + 15) & ~(size_t)15));
+    int* hcnt = reinterpret_cast<int*>(hkey + hot_slots);
+    for (u32 i = threadIdx.x; i < hot_slots; i += blockDim.x) {
+        hkey[i] = HOT_EMPTY;
+        hcnt[i] = 0;
+    }
     const u32 tile_saddr = (PLACE == PLACE_GLOBAL) ? 0u : (u32)__cvta_generic_to_shared(tile);
 
     if (PLACE != PLACE_GLOBAL)
@@ -351,6 +399,13 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                 const u32 valid = __ballot_sync(0xffffffffu, wt[q] != 0);
                 u32 grp = match_key(key[q]) & valid;
                 if (wt[q] != 0) wt[q] = ((grp & ((1u << lane) - 1u)) == 0u) ? __popc(grp) : 0;
+            }
+        }
+        if constexpr (HotKey<typename Ops::key_t>::OK) {
+            if (hot_log2) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (wt[q] != 0 && hot_add(hkey, hcnt, hot_log2, (u64)key[q], wt[q])) wt[q] = 0;
             }
         }
         bool big[4];
@@ -427,9 +482,36 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
         }
     }
 
+    if (PLACE == PLACE_GLOBAL) {
+        if constexpr (HotKey<typename Ops::key_t>::OK) {
+            if (hot_log2) {
+                __syncthreads();
+                for (u32 i = threadIdx.x; i < hot_slots; i += blockDim.x) {
+                    const u64 kw = hkey[i];
+                    const int cnt = hcnt[i];
+                    if (kw == HOT_EMPTY || cnt == 0) continue;
+                    const Prep xq = Ops::prep((typename Ops::key_t)kw);
+                    for (int r = 0; r < t; ++r) {
+                        const int fb = r * NF;
+                        val_t y = MSK_COEF(fb, k - 1);
+                        for (int i2 = k - 2; i2 >= 0; --i2) y = Ops::mul_add(y, xq, MSK_COEF(fb, i2));
+                        const val_t h = Ops::canon(y);
+                        val_t g = h;
+                        if (MODE == CS_TWO_POLY) {
+                            val_t z = MSK_COEF(fb + 1, k - 1);
+                            for (int i2 = k - 2; i2 >= 0; --i2)
+                                z = Ops::mul_add(z, xq, MSK_COEF(fb + 1, i2));
+                            g = Ops::canon(z);
+                        }
+                        apply_update<PLACE>(tile, tile_saddr, a.counters, r, Ops::bucket(h, mask),
+                                            Ops::sign_bit(g), cnt, false, m, log2m, lcs);
+                    }
+                }
+            }
+        }
+        return;
+    }
 #undef MSK_COEF
-
-    if (PLACE == PLACE_GLOBAL) return;
     if (PLACE == PLACE_DSMEM)
         cluster_sync_all();  // every remote add into this block's slice has landed
     else

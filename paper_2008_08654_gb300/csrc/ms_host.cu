@@ -37,6 +37,7 @@ using msi::cuda_fail;
 static const size_t kSmemTileBudget = 112 * 1024;
 static const int kMaxReplicas = 32;   // replicas a large sketch owns (<= 64 MiB)
 static const int kDefaultReplicas = 32;  // replicas a default launch uses
+static const int kHotLog2 = 12;          // hot-key table: 4096 slots (48 KiB) per block
 
 namespace {
 
@@ -468,8 +469,8 @@ extern "C" ms_status cs_coeffs(const cs_sketch* sk, ms_u128* coeffs_host) {
 }
 
 // Launch configuration for one cs_update call (see ms_internal.h).
-ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::UpdateArgs& a,
-                                    msk::LaunchCfg& cfg) {
+ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_weights,
+                                    msk::UpdateArgs& a, msk::LaunchCfg& cfg) {
     const DevInfo d = device_info();
     if (!d.ok) return cuda_fail(cudaGetLastError(), "device query");
     const LaunchOverride& ov = sk->launch;
@@ -527,6 +528,18 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::Update
     a.replicas = cfg.replicas ? sk->replicas : nullptr;
     a.replica_mask = cfg.replicas ? (u32)(cfg.replicas - 1) : 0u;
     a.aggregate = ov.aggregate >= 0 ? ov.aggregate : 1;
+    // Hot-key table (unit weights, one-word keys, global placement): its 12
+    // bytes per slot follow the coefficients in shared memory.  Re-derived after
+    // every change of placement below, so cfg.smem always covers what the
+    // kernel will touch.
+    auto set_hot = [&](bool allow) {
+        const bool on = allow && unit_weights && a.aggregate >= 2 &&
+                        cfg.place == msk::PLACE_GLOBAL && sk->prime != msk::PRIME_89;
+        a.hot_log2 = on ? kHotLog2 : 0;
+        cfg.smem = (cfg.place == msk::PLACE_GLOBAL ? 0 : tile_bytes / cfg.cluster) + extra;
+        if (on) cfg.smem = (cfg.smem + 15) / 16 * 16 + ((size_t)12 << kHotLog2);
+    };
+    set_hot(true);
 
     // resident capacity (the cluster query needs a grid that is a whole cluster)
     cfg.blocks = cfg.cluster;
@@ -538,12 +551,12 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::Update
         // fall back to direct global atomics
         cfg.place = msk::PLACE_GLOBAL;
         cfg.cluster = 1;
-        cfg.smem = extra;
         cfg.blocks = 1;
         cfg.replicas = sk->nrep < kDefaultReplicas ? sk->nrep : kDefaultReplicas;
         a.cluster_log2 = 0;
         a.replicas = cfg.replicas ? sk->replicas : nullptr;
         a.replica_mask = cfg.replicas ? (u32)(cfg.replicas - 1) : 0u;
+        set_hot(true);
         e = msk::query_cs_update_occupancy(sk->prime, a, sk->words.data(), cfg, &occ);
         if (e != cudaSuccess || occ < 1) return cuda_fail(e, "occupancy");
     }
@@ -583,11 +596,11 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, msk::Update
         // even unit weights could overflow an int32 counter: int64 atomics only
         cfg.place = msk::PLACE_GLOBAL;
         cfg.cluster = 1;
-        cfg.smem = extra;
         cfg.replicas = 0;
         a.cluster_log2 = 0;
         a.replicas = nullptr;
         a.replica_mask = 0;
+        set_hot(false);  // per-block counts could overflow int32 too
     }
     return MS_OK;
 }
@@ -603,7 +616,7 @@ extern "C" ms_status cs_update(cs_sketch* sk, const void* keys_dev, const int32_
     memset(&a, 0, sizeof(a));
     msk::LaunchCfg cfg;
     memset(&cfg, 0, sizeof(cfg));
-    ms_status st = choose_update_config(sk, n, a, cfg);
+    ms_status st = choose_update_config(sk, n, weights_dev == nullptr, a, cfg);
     if (st != MS_OK) return st;
     a.keys = keys_dev;
     a.weights = weights_dev;
@@ -769,7 +782,7 @@ extern "C" ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int t
         (threads < 32 || threads > 512 || threads % 32 != 0))
         return MS_ERR_INVALID_ARG;
     if (cluster > 16 || (cluster > 0 && (cluster & (cluster - 1)) != 0)) return MS_ERR_INVALID_ARG;
-    if (replicas > 32 || (replicas > 0 && (replicas & (replicas - 1)) != 0) || aggregate > 1)
+    if (replicas > 32 || (replicas > 0 && (replicas & (replicas - 1)) != 0) || aggregate > 2)
         return MS_ERR_INVALID_ARG;
     sk->launch.place = place;
     sk->launch.strategy = strategy;

@@ -46,6 +46,6 @@ size_t key_bytes(int prime);
 bool less_than_p(msk::u64 lo, msk::u64 hi, int b, uint64_t c);
 void draw_uniform_below_p(int b, uint64_t c, uint64_t seed, int nvals, msk::u64* out);
 ms_status dev_alloc(void** p, size_t bytes);
-ms_status choose_update_config(const cs_sketch* sk, uint64_t n, msk::UpdateArgs& a,
-                               msk::LaunchCfg& cfg);
+ms_status choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_weights,
+                               msk::UpdateArgs& a, msk::LaunchCfg& cfg);
 }  // namespace msi

@@ -46,6 +46,8 @@ struct UpdateArgs {
                              // or NULL for direct int64 atomics
     u32 replica_mask;        // R - 1 (R a power of two)
     int aggregate;           // PLACE_GLOBAL, unit weights: merge equal keys of a warp
+    int hot_log2;            // PLACE_GLOBAL, unit weights: log2 slots of the per-block
+                             // hot-key table in shared memory (0 = none)
 };
 
 // Launch configuration chosen on the host.

@@ -337,7 +337,7 @@ def test_many_sketches_same_stream_differ_only_by_seed(env):
 
 
 @pytest.mark.parametrize("place,replicas,aggregate", [(2, 1, 1), (2, 4, 0), (2, 32, 1), (3, 0, 1),
-                                                      (2, 16, 1)])
+                                                      (2, 16, 1), (2, 32, 2), (3, 0, 2), (2, 1, 2)])
 @pytest.mark.parametrize("b,c", [(61, 1), (31, 1), (89, 1)])
 def test_global_replicas_and_warp_aggregation(env, place, replicas, aggregate, b, c):
     """Zipf keys (many equal keys per warp), unit weights, a sketch too large for
@@ -361,3 +361,29 @@ def test_global_replicas_and_warp_aggregation(env, place, replicas, aggregate, b
     want = oracle.cs_update(b, c, k, t, m, 0, coeffs, keys)
     assert np.array_equal(C, want)
     assert sk.f2() == oracle.f2_estimate(want)
+
+
+@pytest.mark.parametrize("b,c", [(61, 1), (64, 59), (31, 1)])
+def test_hot_key_table_with_sentinel_and_collisions(env, b, c):
+    """Unit weights through the per-block hot-key table: a few very hot keys,
+    the table's EMPTY value itself (all ones) as a hot key, and many cold keys
+    that collide in the table; counters must be exact."""
+    torch, ms = env
+    n = 300007
+    rng = np.random.default_rng(b)
+    if b == 31:
+        cold = datagen.u32_below(3, 0, n)
+        hot = np.array([0xFFFFFFFF, 1, 2, 7, 1 << 31], dtype=np.uint32)
+    else:
+        cold = datagen.u64_below(3, 0, n)
+        hot = np.array([(1 << 64) - 1, 1, 2, 7, 1 << 63], dtype=np.uint64)
+    pick = rng.random(n) < 0.4
+    keys = cold.copy()
+    keys[pick] = hot[rng.integers(0, len(hot), int(pick.sum()))]
+    for blocks in (0, 3):
+        sk = ms.Sketch(t=7, m=1 << 15, k=4, b=b, c=c, seed=5)
+        sk.set_launch(place=2, aggregate=2, blocks=blocks)
+        sk.update(to_dev(torch, keys))
+        C = sk.counters().cpu().numpy()
+        want = oracle.cs_update(b, c, 4, 7, 1 << 15, 0, oracle.sketch_coeffs(b, c, 4, 7, 0, 5), keys)
+        assert np.array_equal(C, want)
