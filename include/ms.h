@@ -293,9 +293,10 @@ ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* th
  *             multiplication, high 64 bits by __umul64hi) -- the unit the
  *             hashing roofline is counted in.
  *  variant 1: one 32x32->64 multiply-add (mad.wide.u32), the partial product
- *             the limb arithmetic is built of.
- *  variant 2: one 32-bit multiply-add (low word only).
- *  variant 3: one 32-bit integer add.
+ *             the limb arithmetic is built of; its multiplicand is the previous
+ *             result, so the product cannot be hoisted out of the loop.
+ *  variant 2: one dependent 32-bit multiply-add (low word only).
+ *  variant 3: one 32-bit integer add (two dependent adds per step, both counted).
  */
 ms_status ms_probe_mul128(int variant, int iters, uint64_t* sink_dev, double* rate, double* ms);
 

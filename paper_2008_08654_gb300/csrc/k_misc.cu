@@ -404,10 +404,11 @@ cudaError_t launch_divmod(int prime, const ms_u128* v, ms_u128* q, void* r, u64 
 // folded into one checksum so nothing can be removed.
 //  variant 0: a <- lo64(a*b) ^ hi64(a*b): one full 64x64->128 product (low half
 //             by multiplication, high half by __umul64hi) per step
-//  variant 1: w <- x*b + w (mad.wide.u32): one 32x32->64 multiply-add per step,
-//             chained only through the 64-bit addend
-//  variant 2: x <- y*b + x (mad.lo.u32): one 32-bit multiply-add per step
-//  variant 3: x <- x + y (add.u32): one 32-bit add per step
+//  variant 1: w <- lo32(w)*b + w (mad.wide.u32): one 32x32->64 multiply-add per
+//             step whose multiplicand is the previous result, so the compiler
+//             cannot hoist the product out of the loop
+//  variant 2: x <- x*b + y (mad.lo.u32): one dependent 32-bit multiply-add
+//  variant 3: x <- x + y; y <- y + x (add.u32): two dependent 32-bit adds
 __global__ void __launch_bounds__(256) k_probe(int variant, int iters, u64 seed, u64* sink) {
     u64 a[8], wv[8];
     u32 x[8], y[8];
@@ -429,23 +430,26 @@ __global__ void __launch_bounds__(256) k_probe(int variant, int iters, u64 seed,
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-                asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(wv[c]) : "r"(x[c]), "r"(b32));
+                asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(wv[c]) : "r"((u32)wv[c]), "r"(b32));
         }
     } else if (variant == 2) {
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-                asm volatile("mad.lo.u32 %0, %1, %2, %0;" : "+r"(x[c]) : "r"(y[c]), "r"(b32));
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[c]) : "r"(b32), "r"(y[c]));
         }
     } else {
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) asm volatile("add.u32 %0, %0, %1;" : "+r"(x[c]) : "r"(y[c]));
+            for (int c = 0; c < 8; ++c) {
+                asm volatile("add.u32 %0, %0, %1;" : "+r"(x[c]) : "r"(y[c]));
+                asm volatile("add.u32 %0, %0, %1;" : "+r"(y[c]) : "r"(x[c]));
+            }
         }
     }
     u64 s = 0;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) s ^= a[c] ^ wv[c] ^ x[c];
+    for (int c = 0; c < 8; ++c) s ^= a[c] ^ wv[c] ^ x[c] ^ ((u64)y[c] << 32);
     if (s == 0x1234567ull) *sink = s;  // practically never taken; keeps the work live
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicXor(sink, s);
 }
@@ -475,7 +479,7 @@ cudaError_t run_probe_mul128(int variant, int iters, u64* sink, double* rate, do
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const double ops = (double)blocks * 256.0 * 8.0 * (double)iters;
+    const double ops = (double)blocks * 256.0 * 8.0 * (double)iters * (variant == 3 ? 2.0 : 1.0);
     *ms = t;
     *rate = ops / (t * 1e-3);
     return cudaSuccess;

@@ -126,6 +126,8 @@ struct ParamCoef {
     u64 w[NFUN > 0 ? NFUN * K * FieldOps<F>::WORDS : 1];
     u32 lo[NFUN > 0 ? NFUN * K : 1];  // P61 only: a & (2^31-1)
     u32 hi[NFUN > 0 ? NFUN * K : 1];  // P61 only: a >> 31
+    int nd[NFUN > 0 ? NFUN * K : 1];  // P61 only: lo - hi
+    u32 c2p31, c4;                    // 2^31 and 4, as run-time operands
 };
 
 // Coefficient a_i of function f.  Generic kernels read the shared-memory copy
@@ -319,6 +321,87 @@ __device__ __forceinline__ void apply_update(int* tile, u32 tile_saddr, long lon
     }
 }
 
+// Counter update on the unchecked path: |w| is within the tile's safe range.
+// A zero delta is still added to shared memory (cheaper than a test); the
+// global placements skip it.
+template <int PLACE>
+__device__ __forceinline__ void apply_fast(int* tile, u32 tile_saddr, long long* counters, int row,
+                                           u32 bucket, int d, int log2m, int lcs) {
+    if (PLACE == PLACE_SMEM) {
+        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(tile_saddr + ((((u32)row << log2m) + bucket) << 2)),
+                     "r"(d)
+                     : "memory");
+    } else if (PLACE == PLACE_DSMEM) {
+        const int lshift = log2m - lcs;
+        const u32 owner = bucket >> lshift;
+        const u32 local = ((u32)row << lshift) + (bucket & ((1u << lshift) - 1u));
+        dsmem_add(tile_saddr + local * 4u, owner, d);
+    } else if (d != 0) {
+        if (tile)
+            atomicAdd(tile + (row << log2m) + bucket, d);
+        else
+            global_add64(counters + (((u64)row) << log2m) + bucket, (long long)d);
+    }
+}
+
+// Bucket and sign bit of row r for p = 2^61-1, k = 4 (Karatsuba power sum):
+// two-for-one (both from one polynomial) or two polynomials (the sign from the
+// second one's bit 60).
+template <int NF, class PC>
+__device__ __forceinline__ void p61_row_bs(const msf::P61::Pow3& xp, const PC& pc, int r, u32 mask,
+                                           u32& bucket, u32& sign) {
+    typedef msf::P61 F;
+    const int fb = r * NF;
+    u32 ylo, yhi;
+    {
+        const u32 al[3] = {pc.lo[fb * 4 + 1], pc.lo[fb * 4 + 2], pc.lo[fb * 4 + 3]};
+        const u32 ah[3] = {pc.hi[fb * 4 + 1], pc.hi[fb * 4 + 2], pc.hi[fb * 4 + 3]};
+        const int nd[3] = {pc.nd[fb * 4 + 1], pc.nd[fb * 4 + 2], pc.nd[fb * 4 + 3]};
+        F::row_kara(xp, al, ah, nd, pc.w[fb * 4], pc.c2p31, pc.c4, ylo, yhi);
+    }
+    F::bucket_sign_hl(ylo, yhi, mask, bucket, sign);
+    if (NF == 2) {
+        const int fs = fb + 1;
+        const u32 sl[3] = {pc.lo[fs * 4 + 1], pc.lo[fs * 4 + 2], pc.lo[fs * 4 + 3]};
+        const u32 sh[3] = {pc.hi[fs * 4 + 1], pc.hi[fs * 4 + 2], pc.hi[fs * 4 + 3]};
+        const int sn[3] = {pc.nd[fs * 4 + 1], pc.nd[fs * 4 + 2], pc.nd[fs * 4 + 3]};
+        u32 unused;
+        F::row_kara(xp, sl, sh, sn, pc.w[fs * 4], pc.c2p31, pc.c4, ylo, yhi);
+        F::bucket_sign_hl(ylo, yhi, mask, unused, sign);
+    }
+}
+
+// One key whose weight could overflow an int32 tile counter (|w| > w_safe):
+// every row is hashed by Horner from the device copy of the coefficients and
+// added to the int64 counters.  Rolled loops keep this rare path small.
+template <class F, int NF>
+__device__ __forceinline__ void update_big_key(const typename FieldOps<F>::Prep& xq, int w,
+                                               const u64* coef, int t, int k, int log2m,
+                                               long long* counters) {
+    typedef FieldOps<F> Ops;
+    typedef typename Ops::val_t val_t;
+    constexpr int W = Ops::WORDS;
+    const u32 mask = (1u << log2m) - 1u;
+#pragma unroll 1
+    for (int r = 0; r < t; ++r) {
+        const u64* cb = coef + (size_t)r * NF * k * W;
+        val_t y = Ops::from_words(cb + (size_t)(k - 1) * W);
+#pragma unroll 1
+        for (int i = k - 2; i >= 0; --i) y = Ops::mul_add(y, xq, Ops::from_words(cb + (size_t)i * W));
+        const val_t h = Ops::canon(y);
+        val_t g = h;
+        if (NF == 2) {
+            const u64* cs = cb + (size_t)k * W;
+            val_t z = Ops::from_words(cs + (size_t)(k - 1) * W);
+#pragma unroll 1
+            for (int i = k - 2; i >= 0; --i) z = Ops::mul_add(z, xq, Ops::from_words(cs + (size_t)i * W));
+            g = Ops::canon(z);
+        }
+        const long long d = Ops::sign_bit(g) ? -(long long)w : (long long)w;
+        global_add64(counters + ((u64)r << log2m) + Ops::bucket(h, mask), d);
+    }
+}
+
 // T, K > 0: compile-time rows and degree with ParamCoef; T = K = 0: runtime t
 // and k with coefficients staged from coef_dev into shared memory.
 // Two-for-one kernels are capped at 64 registers (two 512-thread blocks per SM);
@@ -417,36 +500,46 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
 
         if constexpr (!GENERIC && STRAT == STRAT_POWER_SUM && std::is_same<F, msf::P61>::value &&
                       K == 4) {
-            // x, x^2, x^3 once per key, shared by every row's polynomial(s).
-            typename msf::P61::Split xp[4][3];
+            // Keys whose weight could overflow an int32 tile counter (rare)
+            // go straight to the int64 counters; the hot loops below see
+            // them with weight 0.
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const u64 x1 = msf::P61::reduce_key(key[q]);
-                xp[q][0] = msf::P61::split(x1);
-                const u64 x2 = msf::P61::mul_add(x1, xp[q][0], 0ull);
-                xp[q][1] = msf::P61::split(x2);
-                const u64 x3 = msf::P61::mul_add(x2, xp[q][0], 0ull);
-                xp[q][2] = msf::P61::split(x3);
+                if (big[q]) {
+                    update_big_key<F, NF>(Ops::prep(key[q]), wt[q], a.coef_dev, t, k, log2m,
+                                          a.counters);
+                    wt[q] = 0;
+                }
             }
+            if constexpr (PLACE == PLACE_GLOBAL) {
+                // rows outer: the four keys' atomics of a row go out together
+                msf::P61::Pow3 xp[4];
 #pragma unroll
-            for (int r = 0; r < T; ++r) {
-                const int fb = r * NF;
+                for (int q = 0; q < 4; ++q) msf::P61::powers3(key[q], xp[q]);
+#pragma unroll
+                for (int r = 0; r < T; ++r) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        u32 bucket, sb;
+                        p61_row_bs<NF>(xp[q], pc, r, mask, bucket, sb);
+                        apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket,
+                                          sb ? -wt[q] : wt[q], log2m, lcs);
+                    }
+                }
+            } else {
+                // keys outer: one key's powers live at a time
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const u32 al[3] = {pc.lo[fb * 4 + 1], pc.lo[fb * 4 + 2], pc.lo[fb * 4 + 3]};
-                    const u32 ah[3] = {pc.hi[fb * 4 + 1], pc.hi[fb * 4 + 2], pc.hi[fb * 4 + 3]};
-                    u32 bucket, sb;
-                    msf::P61::power_sum_bs(xp[q], pc.w[fb * 4], al, ah, mask, bucket, sb);
-                    if (MODE == CS_TWO_POLY) {
-                        const int fs = fb + 1;
-                        const u32 sl[3] = {pc.lo[fs * 4 + 1], pc.lo[fs * 4 + 2], pc.lo[fs * 4 + 3]};
-                        const u32 sh[3] = {pc.hi[fs * 4 + 1], pc.hi[fs * 4 + 2], pc.hi[fs * 4 + 3]};
-                        u32 unused;
-                        msf::P61::power_sum_bs(xp[q], pc.w[fs * 4], sl, sh, mask, unused, sb);
+                    msf::P61::Pow3 xp;
+                    msf::P61::powers3(key[q], xp);
+                    const int w = wt[q], w2 = -2 * w;
+#pragma unroll
+                    for (int r = 0; r < T; ++r) {
+                        u32 bucket, sb;
+                        p61_row_bs<NF>(xp, pc, r, mask, bucket, sb);
+                        apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket, (int)sb * w2 + w,
+                                          log2m, lcs);
                     }
-                    if (wt[q] != 0)
-                        apply_update<PLACE>(tile, tile_saddr, a.counters, r, bucket, sb, wt[q],
-                                            big[q], m, log2m, lcs);
                 }
             }
         } else {

@@ -15,9 +15,12 @@ namespace msk {
 template <class F, int NFUN, int K>
 static void fill_param_coef(ParamCoef<F, NFUN, K>& pc, const u64* words) {
     constexpr int W = FieldOps<F>::WORDS;
+    pc.c2p31 = 0x80000000u;
+    pc.c4 = 4u;
     if (NFUN == 0) {
         pc.w[0] = 0;
         pc.lo[0] = pc.hi[0] = 0;
+        pc.nd[0] = 0;
         return;
     }
     for (int i = 0; i < NFUN * K * W; ++i) pc.w[i] = words[i];
@@ -25,6 +28,7 @@ static void fill_param_coef(ParamCoef<F, NFUN, K>& pc, const u64* words) {
         const u64 a = words[i * W];
         pc.lo[i] = (u32)(a & 0x7FFFFFFFull);
         pc.hi[i] = (u32)(a >> 31);
+        pc.nd[i] = (int)pc.lo[i] - (int)pc.hi[i];
     }
 }
 

@@ -148,6 +148,126 @@ struct P61 {
         const u64 S = fold(A) + H + (M >> 30) + ((M & 0x3FFFFFFFull) << 31);
         bucket_sign(fold(S), mask, bucket, sign);
     }
+
+    // ---- Karatsuba power sum (the update kernels' row hash) ----
+    //
+    // Splits of x, x^2, x^3, each lazy (< 2^61 + 8): lo < 2^31, hi <= 2^30,
+    // d = hi - lo (a signed 32-bit value).
+    struct Pow3 {
+        u32 lo[3], hi[3];
+        int d[3];
+    };
+
+    __device__ static __forceinline__ void split3(u64 z, Pow3& xp, int i) {
+        xp.lo[i] = (u32)z & 0x7FFFFFFFu;
+        xp.hi[i] = (u32)(z >> 31);
+        xp.d[i] = (int)xp.hi[i] - (int)xp.lo[i];
+    }
+
+    // x^2 for x = xh 2^31 + xl (lazy):
+    //   x^2 = xh^2 2^62 + xh xl 2^32 + xl^2 = 2 xh^2 + xl^2 + Q 2^32 with Q = xh xl
+    //   Q 2^32 = (Q >> 29) 2^61 + (Q mod 2^29) 2^32 = (Q >> 29) + (Q mod 2^29) 2^32
+    //   sum < 2^62 + 2^61 + 2^32 + 2^61 < 2^64; one fold gives < 2^61 + 4.
+    __device__ static __forceinline__ u64 square(u32 xl, u32 xh) {
+        u64 A = madw(xl, xl, 0ull);
+        A = madw(xh << 1, xh, A);
+        const u64 Q = madw(xh, xl, 0ull);
+        return fold(A + (Q >> 29) + ((Q & 0x1FFFFFFFull) << 32));
+    }
+
+    // x = key mod p (lazy: (key & p) + (key >> 61) < 2^61 + 8), then x^2 and
+    // x^3 = x^2 * x, all three split.  The power-sum bounds below hold for lazy
+    // values, so no canonical reduction is needed here.
+    __device__ static __forceinline__ void powers3(u64 key, Pow3& xp) {
+        const u64 x1 = fold(key);
+        split3(x1, xp, 0);
+        const u64 x2 = square(xp.lo[0], xp.hi[0]);
+        split3(x2, xp, 1);
+        Split s1;
+        s1.lo = xp.lo[0];
+        s1.hi = xp.hi[0];
+        s1.hi2 = xp.hi[0] << 1;
+        split3(mul_add(x2, s1, 0ull), xp, 2);
+    }
+
+    // One row: y = a0 + a1 x + a2 x^2 + a3 x^3 (mod p), lazy (< 2^61 + 8).
+    // With a_i = ah 2^31 + al and x^i = xh 2^31 + xl (2^62 = 2 mod p):
+    //   a_i x^i = al xl + 2 ah xh + (ah xl + al xh) 2^31
+    // and the cross terms by Karatsuba, three 32x32->64 products per term:
+    //   ah xl + al xh = al xl + ah xh + (al - ah)(xh - xl)
+    // Over the three terms (al < 2^31, ah < 2^30, xl < 2^31, xh <= 2^30):
+    //   A = sum al xl < 3 2^62,  H = sum ah xh < 3 2^60,
+    //   M = A + H + sum (al - ah)(xh - xl) = sum (ah xl + al xh) < 3 2^62
+    // (the signed products wrap modulo 2^64; M itself fits, so M is exact).
+    //   M 2^31 = 4 M.hi + (M.lo >> 30) + (M.lo mod 2^30) 2^31          (mod p)
+    //   A      = (A.hi mod 2^29 : A.lo) + (A.hi >> 29)                 (mod p)
+    //   S = (A.hi mod 2^29 : A.lo) + (M.lo mod 2^30) 2^31 + 4 M.hi + 2H
+    //       + (A.hi >> 29) + (M.lo >> 30) + a0
+    //     < 2^61 + 2^61 + 2^34 + 3 2^61 + 2^4 + 2^61 < 2^64
+    //   y = (S.hi mod 2^29 : S.lo) + (S.hi >> 29) < 2^61 + 8.
+    // c2p31 = 2^31 and c4 = 4 arrive as run-time operands so that both
+    // shift-adds stay wide multiply-adds.
+    __device__ static __forceinline__ void row_kara(const Pow3& xp, const u32* al, const u32* ah,
+                                                    const int* nd, u64 a0, u32 c2p31, u32 c4,
+                                                    u32& ylo, u32& yhi) {
+        asm("{\n\t"
+            ".reg .u64 A, H, E, M, T;\n\t"
+            ".reg .u32 Al, Ah, Ml, Mh, m0, m1, zA, zm, Tl, Th, z;\n\t"
+            "mul.wide.u32 A, %2, %11;\n\t"
+            "mad.wide.u32 A, %3, %14, A;\n\t"
+            "mad.wide.u32 A, %4, %17, A;\n\t"
+            "mul.wide.u32 H, %5, %12;\n\t"
+            "mad.wide.u32 H, %6, %15, H;\n\t"
+            "mad.wide.u32 H, %7, %18, H;\n\t"
+            "mul.wide.s32 E, %8, %13;\n\t"
+            "mad.wide.s32 E, %9, %16, E;\n\t"
+            "mad.wide.s32 E, %10, %19, E;\n\t"
+            "add.u64 M, A, H;\n\t"
+            "add.u64 M, M, E;\n\t"
+            "mov.b64 {Ml, Mh}, M;\n\t"
+            "and.b32 m0, Ml, 0x3FFFFFFF;\n\t"
+            "shr.u32 m1, Ml, 30;\n\t"
+            "mov.b64 {Al, Ah}, A;\n\t"
+            "shr.u32 zA, Ah, 29;\n\t"
+            "and.b32 Ah, Ah, 0x1FFFFFFF;\n\t"
+            "mov.b64 T, {Al, Ah};\n\t"
+            "mad.wide.u32 T, m0, %22, T;\n\t"
+            "mad.wide.u32 T, Mh, %23, T;\n\t"
+            "add.u64 T, T, H;\n\t"
+            "add.u64 T, T, H;\n\t"
+            "add.u32 zm, zA, m1;\n\t"
+            "mov.b64 {Tl, Th}, T;\n\t"
+            "add.cc.u32 Tl, Tl, zm;\n\t"
+            "addc.u32 Th, Th, 0;\n\t"
+            "add.cc.u32 Tl, Tl, %20;\n\t"
+            "addc.u32 Th, Th, %21;\n\t"
+            "shr.u32 z, Th, 29;\n\t"
+            "and.b32 Th, Th, 0x1FFFFFFF;\n\t"
+            "add.cc.u32 %0, Tl, z;\n\t"
+            "addc.u32 %1, Th, 0;\n\t"
+            "}"
+            : "=r"(ylo), "=r"(yhi)
+            : "r"(al[0]), "r"(al[1]), "r"(al[2]), "r"(ah[0]), "r"(ah[1]), "r"(ah[2]), "r"(nd[0]),
+              "r"(nd[1]), "r"(nd[2]), "r"(xp.lo[0]), "r"(xp.hi[0]), "r"(xp.d[0]), "r"(xp.lo[1]),
+              "r"(xp.hi[1]), "r"(xp.d[1]), "r"(xp.lo[2]), "r"(xp.hi[2]), "r"(xp.d[2]), "r"((u32)a0),
+              "r"((u32)(a0 >> 32)), "r"(c2p31), "r"(c4));
+    }
+
+    // Bucket and sign bit of the canonical residue of a lazy y = (yhi:ylo)
+    // < 2^61 + 8.  Only y in [p, 2^61 + 8) needs the subtraction (then
+    // yhi >= 0x1FFFFFFF; the result is below 9, sign 0).  Otherwise yhi < 2^29
+    // and bit 60 is yhi >> 28.
+    __device__ static __forceinline__ void bucket_sign_hl(u32 ylo, u32 yhi, u32 mask, u32& bucket,
+                                                          u32& sign) {
+        if (yhi >= 0x1FFFFFFFu) {
+            u64 y = ((u64)yhi << 32) | ylo;
+            y = canon(y);
+            ylo = (u32)y;
+            yhi = (u32)(y >> 32);
+        }
+        bucket = ylo & mask;
+        sign = yhi >> 28;
+    }
 };
 
 // ---------------------------------------------------------------- p = 2^31-1
