@@ -19,9 +19,11 @@
 
 namespace msk {
 
-struct PsCoef {  // one polynomial, power-sum form (p = 2^61-1, k = 4)
+struct PsCoef {  // one polynomial, Karatsuba power-sum form (p = 2^61-1, k = 4)
     u64 a0;
     u32 lo[3], hi[3];
+    int nd[3];  // lo - hi
+    u32 pad;
 };
 
 // C[r][bucket] += sign ? -w : w, into the item's tile (rows r0..) or, for
@@ -89,7 +91,9 @@ __global__ void __launch_bounds__(512) k_cs_update_batched(const BatchArgs a) {
                 for (int i = 0; i < 3; ++i) {
                     pc.lo[i] = (u32)(c[i + 1] & 0x7FFFFFFFull);
                     pc.hi[i] = (u32)(c[i + 1] >> 31);
+                    pc.nd[i] = (int)pc.lo[i] - (int)pc.hi[i];
                 }
+                pc.pad = 0;
                 sps[f] = pc;
             }
         }
@@ -110,29 +114,25 @@ __global__ void __launch_bounds__(512) k_cs_update_batched(const BatchArgs a) {
                 big[q] = !use_tile || aw > w_safe;
             }
             if constexpr (PS) {
-                typename msf::P61::Split xp[4][3];
+                msf::P61::Pow3 xp[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const u64 x1 = msf::P61::reduce_key(key[q]);
-                    xp[q][0] = msf::P61::split(x1);
-                    const u64 x2 = msf::P61::mul_add(x1, xp[q][0], 0ull);
-                    xp[q][1] = msf::P61::split(x2);
-                    const u64 x3 = msf::P61::mul_add(x2, xp[q][0], 0ull);
-                    xp[q][2] = msf::P61::split(x3);
-                }
+                for (int q = 0; q < 4; ++q) msf::P61::powers3(key[q], xp[q]);
                 for (int r = r0; r < r1; ++r) {
                     const PsCoef cb = sps[(r - r0) * NF];
                     PsCoef cs;
                     if (MODE == CS_TWO_POLY) cs = sps[(r - r0) * NF + 1];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const u64 h = msf::P61::power_sum<3>(xp[q], cb.a0, cb.lo, cb.hi);
-                        const u32 sb = (MODE == CS_TWO_POLY)
-                                           ? msf::P61::sign_bit(msf::P61::power_sum<3>(xp[q], cs.a0, cs.lo, cs.hi))
-                                           : msf::P61::sign_bit(h);
+                        u32 ylo, yhi, bucket, sb;
+                        msf::P61::row_kara(xp[q], cb.lo, cb.hi, cb.nd, cb.a0, a.c2p31, a.c4, ylo, yhi);
+                        msf::P61::bucket_sign_hl(ylo, yhi, mask, bucket, sb);
+                        if (MODE == CS_TWO_POLY) {
+                            u32 unused;
+                            msf::P61::row_kara(xp[q], cs.lo, cs.hi, cs.nd, cs.a0, a.c2p31, a.c4, ylo, yhi);
+                            msf::P61::bucket_sign_hl(ylo, yhi, mask, unused, sb);
+                        }
                         if (wt[q] != 0)
-                            batched_add(tile, job.counters, r, r0, log2m, msf::P61::bucket(h, mask),
-                                        sb, wt[q], big[q]);
+                            batched_add(tile, job.counters, r, r0, log2m, bucket, sb, wt[q], big[q]);
                     }
                 }
             } else {

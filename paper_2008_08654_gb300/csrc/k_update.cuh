@@ -460,6 +460,8 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
     const u64 n = a.n;
     const bool vec = a.vec_ok != 0;
     const u32 w_safe = a.w_safe;
+    const bool unit_safe = a.weights == nullptr && w_safe >= 1u;  // every weight is 0 or 1
+    const u32 row_bytes = m << 2;  // PLACE_SMEM: one row of the int32 tile
     const u64 stride = (u64)gridDim.x * blockDim.x * 4ull;
     // The loop runs on the warp's first key index, so every lane of a warp takes
     // the same number of iterations (lanes past the end load weight-0 keys);
@@ -495,7 +497,7 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const u32 aw = wt[q] < 0 ? 0u - (u32)wt[q] : (u32)wt[q];
-            big[q] = aw > w_safe;
+            big[q] = !unit_safe && aw > w_safe;
         }
 
         if constexpr (!GENERIC && STRAT == STRAT_POWER_SUM && std::is_same<F, msf::P61>::value &&
@@ -533,12 +535,19 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                     msf::P61::Pow3 xp;
                     msf::P61::powers3(key[q], xp);
                     const int w = wt[q], w2 = -2 * w;
+                    u32 rbase = tile_saddr;  // shared address of row r's counters
 #pragma unroll
                     for (int r = 0; r < T; ++r) {
                         u32 bucket, sb;
                         p61_row_bs<NF>(xp, pc, r, mask, bucket, sb);
-                        apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket, (int)sb * w2 + w,
-                                          log2m, lcs);
+                        const int d = (int)sb * w2 + w;
+                        if (PLACE == PLACE_SMEM) {
+                            asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(rbase + (bucket << 2)), "r"(d)
+                                         : "memory");
+                            rbase += row_bytes;
+                        } else {
+                            apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket, d, log2m, lcs);
+                        }
                     }
                 }
             }

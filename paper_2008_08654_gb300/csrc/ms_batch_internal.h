@@ -32,6 +32,7 @@ struct BatchArgs {
     u32 chunk;           // keys per work item
     u32 smem_min_ratio;  // shared-memory tile when chunk keys >= ratio * m
     u32 w_safe;          // |w| <= w_safe may use int32 tile counters
+    u32 c2p31 = 0x80000000u, c4 = 4u;  // run-time operands of the p = 2^61-1 row hash
 };
 
 struct BatchLaunch {

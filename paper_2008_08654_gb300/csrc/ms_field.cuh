@@ -68,7 +68,8 @@ struct P61 {
     __device__ static __forceinline__ u64 fold(u64 S) { return (S & P) + (S >> 61); }
 
     // One Horner step (Algorithm Mersenne): returns y = z*x + a (mod p), lazily
-    // reduced (< 2^61 + 8), for z < 2^61 + 8, x canonical (xs = split(x)),
+    // reduced (< 2^61 + 8), for z, x < 2^61 + 8 (xs = split(x); lazy values
+    // keep zh, xh <= 2^30 and zl, xl < 2^31, which is all the bounds use),
     // a < 2^61.
     //   z*x = zh*xh*2^62 + (zh*xl + zl*xh)*2^31 + zl*xl,   2^62 = 2 (mod p)
     //   A = zl*xl + a + zh*(2xh)   <= (2^31-1)^2 + 2^61 + 2^30*(2^31-2) < 2^63
@@ -86,31 +87,6 @@ struct P61 {
         return fold(S);
     }
 
-    // Power-sum row hash for k = 4 (Sec. 1.2 definition h = sum a_i x^i):
-    // given splits of x, x^2, x^3 (lazy, < 2^61 + 8) and the row's coefficients
-    // a_0 (full) and split a_1..a_3 (al < 2^31, ah < 2^30):
-    //   A = a_0 + sum al_i*xl_i              < 2^61 + 3*2^62           < 2^64
-    //   H = sum ah_i*(2 xh_i)                <= 3 * 2^30 * 2^31       = 3*2^61
-    //   M = sum (ah_i*xl_i + al_i*xh_i)      < 6 * 2^61               < 2^64
-    //   S = fold(A) + H + (M >> 30) + (M mod 2^30)*2^31
-    //                                         < 2^61+8 + 3*2^61 + 2^34 + 2^61 < 2^64
-    // Returns the canonical hash value.
-    template <int KM1>
-    __device__ static __forceinline__ u64 power_sum(const Split* xp, u64 a0, const u32* al,
-                                                    const u32* ah) {
-        static_assert(KM1 >= 1 && KM1 <= 3, "at most 3 lazy terms per accumulator");
-        u64 A = a0, H = 0, M = 0;
-#pragma unroll
-        for (int i = 0; i < KM1; ++i) {
-            A += (u64)al[i] * xp[i].lo;
-            H += (u64)ah[i] * xp[i].hi2;
-            M += (u64)ah[i] * xp[i].lo;
-            M += (u64)al[i] * xp[i].hi;
-        }
-        const u64 S = fold(A) + H + (M >> 30) + ((M & 0x3FFFFFFFull) << 31);
-        return canon(fold(S));
-    }
-
     __device__ static __forceinline__ u32 bucket(u64 h, u32 mask) { return (u32)h & mask; }
     __device__ static __forceinline__ u32 sign_bit(u64 h) { return (u32)(h >> 60) & 1u; }
 
@@ -119,34 +95,6 @@ struct P61 {
         u64 d;
         asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
         return d;
-    }
-
-    // Bucket and sign bit of the canonical residue of a lazily reduced
-    // y < 2^61 + 8.  Only y in [p, 2^61 + 8) -- at most 9 of those values --
-    // needs the subtraction, and then y.hi >= 0x1FFFFFFF; every other value
-    // takes the short path.
-    __device__ static __forceinline__ void bucket_sign(u64 y, u32 mask, u32& bucket, u32& sign) {
-        if ((u32)(y >> 32) >= 0x1FFFFFFFu) y = canon(y);
-        bucket = (u32)y & mask;
-        sign = (u32)(y >> 60) & 1u;
-    }
-
-    // power_sum<3> returning the bucket and sign bit of the canonical value:
-    // the same accumulators with explicit wide multiply-adds, then the same
-    // two folds (bounds as in power_sum).
-    __device__ static __forceinline__ void power_sum_bs(const Split* xp, u64 a0, const u32* al,
-                                                        const u32* ah, u32 mask, u32& bucket,
-                                                        u32& sign) {
-        u64 A = a0, H = 0, M = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            A = madw(al[i], xp[i].lo, A);
-            H = madw(ah[i], xp[i].hi2, H);
-            M = madw(ah[i], xp[i].lo, M);
-            M = madw(al[i], xp[i].hi, M);
-        }
-        const u64 S = fold(A) + H + (M >> 30) + ((M & 0x3FFFFFFFull) << 31);
-        bucket_sign(fold(S), mask, bucket, sign);
     }
 
     // ---- Karatsuba power sum (the update kernels' row hash) ----
