@@ -506,6 +506,57 @@ def run_div(args):
                  parity_on_sample=bool(ok))
 
 
+# Table 2 (Sec. 5): ms for 10^7 divisions of 2b-bit values by 2^b - 1 on one
+# core of an i7-8850H / a Xeon E5-2690 v4 (Algorithm division-generalized on GMP).
+TABLE2_CPU_MS = {32: (138, 149), 64: (142, 198), 128: (157, 207), 256: (187, 222),
+                 512: (291, 294), 1024: (358, 372)}
+
+
+def run_divwide(args):
+    """Table 2's workload on the GPU: 10^7 divisions of uniform 2b-bit values by
+    p = 2^b - 1 for b in {32, 64, ..., 1024} (ms_div_wide).  Reads 2b bits and
+    writes the (b+1)-bit quotient and b-bit remainder per value."""
+    import torch
+    import oracle
+    import paper_2008_08654_gb300 as ms
+    n = args.keys or 10 ** 7
+    hbm_peak = 6787.9
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        pass
+    rows, ok, last = {}, True, None
+    for b in (32, 64, 128, 256, 512, 1024):
+        lv, lq, lr = (2 * b + 63) // 64, (b + 64) // 64, (b + 63) // 64
+        v = datagen.u64_below(args.seed + b, 0, n * lv, stream=datagen.STREAM_VALUES).reshape(n, lv)
+        if (2 * b) % 64:
+            v[:, -1] &= np.uint64((1 << ((2 * b) % 64)) - 1)
+        vd = torch.from_numpy(v.view(np.int64)).cuda()
+        q = torch.empty((n, lq), dtype=torch.int64, device="cuda")
+        r = torch.empty((n, lr), dtype=torch.int64, device="cuda")
+        t = _timed(lambda: ms.div_wide(b, 1, vd, q=q, r=r), max(1, args.steps), args.warmup)
+        idx = np.unique(datagen.u64_below(args.seed + 1, n, 2048))
+        qw, rw = oracle.divmod_wide(b, 1, v[idx])
+        ok = ok and np.array_equal(q.cpu().numpy()[idx].view(np.uint64), qw) and \
+            np.array_equal(r.cpu().numpy()[idx].view(np.uint64), rw)
+        nbytes = 8 * (lv + lq + lr)
+        gbs = nbytes * n / (t * 1e-3) / 1e9
+        rows["b=%d" % b] = {"ms_per_1e7": t * 1e7 / n, "values_per_s": n / (t * 1e-3),
+                            "bytes_per_value": nbytes, "gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                            "paper_cpu_ms_per_1e7": list(TABLE2_CPU_MS[b])}
+        last = (t, gbs, nbytes)
+        del vd, q, r
+        torch.cuda.empty_cache()
+    t, gbs, nbytes = last
+    return _line("wide ms_div values/s (b=1024, p=2^1024-1)", n / (t * 1e-3), "values/s", args,
+                 {"workload": "%d uniform 2b-bit values per b, b in {32..1024}, p = 2^b - 1" % n,
+                  "l2": "every b's inputs plus outputs exceed the 129 MB L2; no flush"},
+                 ms_per_step=t, roofline={"bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                                          "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+                                          "kernel": "k_divwide", "bytes_per_value": nbytes},
+                 table2=rows, parity_on_sample=bool(ok))
+
+
 def run_table1(args):
     """The paper's Table 1 workload: 10^7 k-universal hashes of random 64-bit
     keys for k in {2, 4, 8}, p = 2^61-1 and p = 2^89-1 (keys in device memory)."""
@@ -647,7 +698,8 @@ def run_serving(args):
                  saturated=peak, offered_load=levels)
 
 
-EXTRA = {"sweep": run_sweep, "div": run_div, "table1": run_table1, "batched": run_batched,
+EXTRA = {"sweep": run_sweep, "div": run_div, "divwide": run_divwide, "table1": run_table1,
+         "batched": run_batched,
          "serving": run_serving}
 
 

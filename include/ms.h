@@ -125,6 +125,27 @@ ms_status ms_div(int b, uint64_t c, const ms_u128* v_dev, ms_u128* q_dev, void* 
 /* ms_mod -- remainders only: r_dev[j] = v_dev[j] mod p (same types as ms_div). */
 ms_status ms_mod(int b, uint64_t c, const ms_u128* v_dev, void* r_dev, size_t n, void* stream);
 
+/*
+ * ms_div_wide -- quotient and remainder of wide values by p = 2^b - c, the
+ * setting of Table 2 (Sec. 5: 2b-bit values, b up to 1024): Algorithm
+ * division-generalized (Sec. 1.6) with ms_div_wide_steps(b, c) steps, which
+ * the theorem of Sec. 4 shows cover every v < 2^(2b), then Algorithm
+ * mod-generalized.  p need not be prime.
+ *  b: 32..1024; c: 1 <= c < 2^32, and c < 2^(b/2) when b <= 64.
+ *  v_dev: n values of ceil(2b/64) uint64 limbs each, little-endian, value-major;
+ *         the value used is v mod 2^(2b) (bits at and above 2b are ignored).
+ *  q_dev: n quotients of ceil((b+1)/64) limbs (floor(v/p) < 2^(b+1)), or NULL.
+ *  r_dev: n remainders of ceil(b/64) limbs, or NULL (not both NULL).
+ *  All three 8-byte aligned.  n == 0 is a no-op.
+ *  Errors: INVALID_ARG (b or c out of range, null buffers), MISALIGNED, CUDA.
+ */
+ms_status ms_div_wide(int b, uint64_t c, const uint64_t* v_dev, uint64_t* q_dev, uint64_t* r_dev,
+                      size_t n, void* stream);
+
+/* Steps ms_div_wide runs for (b, c): 2 for c = 1, else floor(2b / (b - log2 c)) + 1;
+ * -1 when c >= 2^(b-1).  Host only. */
+int ms_div_wide_steps(int b, uint64_t c);
+
 /* ------------------------------------------------------------- Count Sketch */
 
 typedef struct cs_sketch cs_sketch;

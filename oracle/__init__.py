@@ -225,3 +225,44 @@ def exact_f2(keys: np.ndarray, weights=None) -> int:
     out = np.empty(2, dtype=np.uint64)
     _load().or_exact_f2(keys.ctypes.data, _ptr(weights), keys.shape[0], out.ctypes.data)
     return to_int(out)
+
+
+# ------------------------------------------------------------ wide division
+
+def limbs_to_ints(a: np.ndarray) -> list[int]:
+    """(n, L) little-endian uint64 limbs -> Python integers."""
+    a = np.ascontiguousarray(a).view(np.uint64).reshape(a.shape[0], -1)
+    out = []
+    for row in a:
+        v = 0
+        for i in range(len(row) - 1, -1, -1):
+            v = (v << 64) | int(row[i])
+        out.append(v)
+    return out
+
+
+def ints_to_limbs(vals, nlimbs: int) -> np.ndarray:
+    """Python integers (each < 2^(64 nlimbs)) -> (n, nlimbs) uint64 limbs."""
+    out = np.zeros((len(vals), nlimbs), dtype=np.uint64)
+    mask = (1 << 64) - 1
+    for j, v in enumerate(vals):
+        for i in range(nlimbs):
+            out[j, i] = (v >> (64 * i)) & mask
+    return out
+
+
+def divmod_wide(b: int, c: int, v: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Quotient and remainder of wide values by p = 2^b - c, by definition
+    (Python's integer floor division and remainder) -- the operation whose
+    fast form is Algorithm division-generalized + mod-generalized (Sec. 1.6;
+    Table 2 of Sec. 5 times it for 2b-bit values).  v: (n, ceil(2b/64)) limbs;
+    the value used is v mod 2^(2b).  Returns (q, r) as (n, ceil((b+1)/64)) and
+    (n, ceil(b/64)) limb arrays."""
+    p = (1 << b) - c
+    lq, lr = (b + 64) // 64, (b + 63) // 64
+    qs, rs = [], []
+    for x in limbs_to_ints(v):
+        q, r = divmod(x % (1 << (2 * b)), p)
+        qs.append(q)
+        rs.append(r)
+    return ints_to_limbs(qs, lq), ints_to_limbs(rs, lr)

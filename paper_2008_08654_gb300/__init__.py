@@ -71,6 +71,8 @@ def _load():
         "ms_hash_destroy": (i, [vp]),
         "ms_div": (i, [i, u64, vp, vp, vp, sz, vp]),
         "ms_mod": (i, [i, u64, vp, vp, sz, vp]),
+        "ms_div_wide": (i, [i, u64, vp, vp, vp, sz, vp]),
+        "ms_div_wide_steps": (i, [i, u64]),
         "cs_create": (i, [pp, i, u32, i, i, u64, u64, i]),
         "cs_create_coeffs": (i, [pp, i, u32, i, i, u64, i, vp]),
         "cs_destroy": (i, [vp]),
@@ -233,6 +235,32 @@ def mod(b: int, c: int, v: torch.Tensor, r: torch.Tensor | None = None, stream=N
         r = torch.empty((n, 2) if b > 64 else (n,), dtype=torch.int64, device=v.device)
     _check(_load().ms_mod(b, c, _ptr(v), _ptr(r), n, _stream(stream)), "ms_mod")
     return r
+
+
+def div_wide(b: int, c: int, v: torch.Tensor, want_q: bool = True, want_r: bool = True,
+             stream=None, q: torch.Tensor | None = None, r: torch.Tensor | None = None):
+    """Quotient and remainder of wide values by p = 2^b - c (ms_div_wide).
+    v: (n, ceil(2b/64)) int64/uint64 tensor of little-endian limbs.  Returns
+    (q, r) as (n, ceil((b+1)/64)) and (n, ceil(b/64)) int64 tensors (or None);
+    q and r may be passed in preallocated."""
+    lv, lq, lr = (2 * b + 63) // 64, (b + 64) // 64, (b + 63) // 64
+    if v.dim() != 2 or v.shape[1] != lv:
+        raise ValueError("v must have shape (n, %d)" % lv)
+    n = v.shape[0]
+    if want_q and q is None:
+        q = torch.empty((n, lq), dtype=torch.int64, device=v.device)
+    if want_r and r is None:
+        r = torch.empty((n, lr), dtype=torch.int64, device=v.device)
+    q = q if want_q else None
+    r = r if want_r else None
+    _check(_load().ms_div_wide(b, c, _ptr(v), _ptr(q) if q is not None else None,
+                               _ptr(r) if r is not None else None, n, _stream(stream)),
+           "ms_div_wide")
+    return q, r
+
+
+def div_wide_steps(b: int, c: int) -> int:
+    return int(_load().ms_div_wide_steps(b, c))
 
 
 # ------------------------------------------------------------------ sketch
