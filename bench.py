@@ -54,6 +54,9 @@ WORKLOADS = {
                        "[-100,100], t=5, m=1024"),
     "plain-2^28": dict(n=1 << 28, t=5, m=1024, mode=0, keys="uniform", weights="pm100",
                        desc="plain sketch distribution at 2^28 keys"),
+    "plain-anyr": dict(n=1 << 28, t=5, m=1000, mode=2, keys="uniform", weights="pm100",
+                       desc="plain sketch distribution at 2^28 keys, m = 1000 buckets "
+                            "(any-m map of Algorithm Mersenne-arb-r)"),
 }
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"

@@ -106,7 +106,7 @@ ms_status ms_hash_destroy(ms_hash* h);
 
 /*
  * ms_div -- quotient and remainder of 128-bit values by p = 2^b - c, branch
- * free: Algorithm division-generalized (Sec. 1.6; its correctness range is the
+ * free: Algorithm division-generalized (Sec. 1.5; its correctness range is the
  * theorem of Sec. 4) computes z = floor(v / p) with enough steps to cover all
  * of [0, 2^128): (31,1): 5 steps, (61,1): 3, (89,1): 2, (64,59): 3.  For
  * c = 1 and v < 2^(2b) the first two steps are Algorithm div-simple.
@@ -128,7 +128,7 @@ ms_status ms_mod(int b, uint64_t c, const ms_u128* v_dev, void* r_dev, size_t n,
 /*
  * ms_div_wide -- quotient and remainder of wide values by p = 2^b - c, the
  * setting of Table 2 (Sec. 5: 2b-bit values, b up to 1024): Algorithm
- * division-generalized (Sec. 1.6) with ms_div_wide_steps(b, c) steps, which
+ * division-generalized (Sec. 1.5) with ms_div_wide_steps(b, c) steps, which
  * the theorem of Sec. 4 shows cover every v < 2^(2b), then Algorithm
  * mod-generalized.  p need not be prime.
  *  b: 32..1024; c: 1 <= c < 2^32, and c < 2^(b/2) when b <= 64.
@@ -152,22 +152,35 @@ typedef struct cs_sketch cs_sketch;
 
 enum {
     CS_TWO_FOR_ONE = 0, /* bucket and sign from ONE hash value (Algorithm h-and-s) */
-    CS_TWO_POLY = 1     /* bucket from one polynomial, sign from a second one */
+    CS_TWO_POLY = 1,    /* bucket from one polynomial, sign from a second one */
+    CS_ANY_R = 2        /* flag: m need not be a power of two (Sec. 3.3 / Sec. 1.5) */
 };
 
 /*
- * cs_create -- a t-row Count Sketch (Algorithm count-sketch, Sec. 1.4) with
+ * cs_create -- a t-row Count Sketch (Algorithm count-sketch, Sec. 1.3) with
  * m counters per row, each row with its own hash function(s) of degree k-1
  * over p = 2^b - c.
  *  t: odd, 1..15 (the F2 estimate is the median of the t row estimates).
  *  m: power of two, 2 <= m <= 2^24, and m < 2^(b-1) so that the bucket bits
- *     and the sign bit are disjoint (Sec. 1.4).
- *  k: 1..8.  mode: CS_TWO_FOR_ONE or CS_TWO_POLY.
+ *     and the sign bit are disjoint (Sec. 1.3).
+ *  k: 1..8.  mode: CS_TWO_FOR_ONE or CS_TWO_POLY, optionally | CS_ANY_R.
  *  Two-for-one (Algorithm h-and-s): for hash value h of row r,
  *      bucket = h & (m - 1)   (the log2(m) least significant bits)
  *      a      = h >> (b - 1)  (the most significant of the b bits)
  *      sign   = 1 - 2a.
  *  Two-poly: bucket from polynomial P_r as above, a = bit b-1 of Q_r(x).
+ *  CS_ANY_R: m is any number of buckets, 2 <= m <= 2^24 (and m <= 2^(b-2)).
+ *    c = 1 (Algorithm Mersenne-arb-r, Sec. 3.3): h' = h + 1, j = h' mod
+ *      2^(b-1), bucket = floor(m j / 2^(b-1)); in two-for-one mode
+ *      a = floor(h' / 2^(b-1)) and sign = 2a - 1 (the sign convention of that
+ *      section's text and proofs).
+ *    c > 1 (2^64 - 59): bucket = floor(h m / p), the most uniform map of
+ *      Sec. 1.5; there is no sign bit to pair with it, so this needs
+ *      CS_TWO_POLY (else INVALID_ARG).
+ *    With CS_TWO_POLY the sign is always bit b-1 of Q_r(x), as above.
+ *    Storage: rows are cs_row_stride = 2^ceil(log2 m) counters wide; the
+ *    columns from m on stay zero.  Batched plans and the server take only
+ *    power-of-two sketches.
  *  Coefficients: drawn as in ms_hash_init from one SplitMix64 sequence started
  *  at `seed`, in the order row 0 bucket polynomial, row 0 sign polynomial
  *  (two-poly only), row 1 bucket polynomial, ..., each a_0 first.
@@ -184,9 +197,13 @@ ms_status cs_create_coeffs(cs_sketch** out, int t, uint32_t m, int k, int b, uin
 
 ms_status cs_destroy(cs_sketch* sk);
 
-/* Parameters of a sketch; any output pointer may be NULL. */
+/* Parameters of a sketch (m as created); any output pointer may be NULL. */
 ms_status cs_params(const cs_sketch* sk, int* t, uint32_t* m, int* k, int* b, uint64_t* c,
                     int* mode);
+
+/* Counters per row in memory: m, or 2^ceil(log2 m) for CS_ANY_R sketches.
+ * cs_counters, cs_export and cs_import use rows of this width. */
+ms_status cs_row_stride(const cs_sketch* sk, uint32_t* stride);
 
 /* Copies the sketch's coefficients (t*k or 2*t*k ms_u128) to the host. */
 ms_status cs_coeffs(const cs_sketch* sk, ms_u128* coeffs_host);
@@ -241,7 +258,7 @@ ms_status cs_estimate_f2_noalloc(const int64_t* counters_dev, int t, uint32_t m,
 /*
  * cs_point_query -- the estimate of f_x for each key: median over rows r of
  * sign_r(x) * C[r][bucket_r(x)] (the point-query use of the Count Sketch,
- * Sec. 1.4).  out_dev: n int64.  Errors: INVALID_ARG, CUDA.
+ * Sec. 1.3).  out_dev: n int64.  Errors: INVALID_ARG, CUDA.
  */
 ms_status cs_point_query(const cs_sketch* sk, const void* keys_dev, int64_t* out_dev, size_t n,
                          void* stream);
@@ -254,7 +271,7 @@ ms_status cs_reset(cs_sketch* sk, void* stream);
 
 /*
  * cs_merge -- dst += src counter by counter.  A Count Sketch is linear in the
- * stream (Sec. 1.4), so the result is the sketch of the concatenated streams.
+ * stream (Sec. 1.3), so the result is the sketch of the concatenated streams.
  * Both sketches must have identical t, m, k, prime, mode and coefficients,
  * else INVALID_ARG.
  */

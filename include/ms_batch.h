@@ -3,7 +3,7 @@
  * CUDA-graph-captured kernel launch, with a launch-shape autotuner.
  *
  * Not in the paper: this applies Process(x, Delta) of Algorithm count-sketch
- * (Sec. 1.4) to thousands of sketches at once.  Each sketch keeps its own
+ * (Sec. 1.3) to thousands of sketches at once.  Each sketch keeps its own
  * coefficients, t and m; the arithmetic and the result are exactly those of
  * cs_update (include/ms.h) applied job by job, since integer addition commutes.
  *
@@ -48,7 +48,7 @@ ms_status cs_batch_default_tuning(cs_batch_tuning* out);
 /*
  * cs_batch_create -- a reusable plan that applies `count` jobs (host array) in
  * one persistent kernel launch.  All sketches must share the prime, k and mode
- * (else INVALID_ARG).  The job table is copied to the device; the plan owns a
+ * and have a power-of-two number of buckets (no CS_ANY_R; else INVALID_ARG).  The job table is copied to the device; the plan owns a
  * small device allocation (job table and work counter) and a CUDA graph of
  * [work-counter reset, persistent kernel].  The keys, weights and sketches must
  * stay alive while the plan is used.  Errors: INVALID_ARG, MISALIGNED, OOM, CUDA.

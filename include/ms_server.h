@@ -3,7 +3,7 @@
  * over many device-resident sketches.
  *
  * Not in the paper: the serving pattern applied to Process(x, Delta) and
- * Output of Algorithm count-sketch (Sec. 1.4).  Results are exact: a query
+ * Output of Algorithm count-sketch (Sec. 1.3).  Results are exact: a query
  * returns the same 128-bit F2 estimate as cs_estimate_f2 on a sketch that saw
  * exactly the updates submitted to it before the query (per-sketch FIFO),
  * however requests are batched.
@@ -24,7 +24,7 @@ typedef struct ms_server ms_server;
 typedef struct {
     int t, k, b;                  /* rows, polynomial degree + 1, prime 2^b - c */
     uint64_t c;
-    int mode;                     /* CS_TWO_FOR_ONE or CS_TWO_POLY */
+    int mode;                     /* CS_TWO_FOR_ONE or CS_TWO_POLY (no CS_ANY_R) */
     uint64_t seed_base;           /* sketch i is seeded with seed_base + i */
     int num_sketches;
     const uint32_t* m_per_sketch; /* num_sketches widths (host array, copied) */

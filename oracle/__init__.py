@@ -25,6 +25,7 @@ _lib = None
 
 TWO_FOR_ONE = 0
 TWO_POLY = 1
+ANY_R = 2  # mode flag: any number of buckets m (not only powers of two)
 
 
 def build(force: bool = False) -> str:
@@ -121,7 +122,7 @@ def draw_coeffs(b: int, c: int, k: int, nfun: int, seed: int) -> np.ndarray:
 def sketch_coeffs(b: int, c: int, k: int, t: int, mode: int, seed: int) -> np.ndarray:
     """Coefficients of a t-row sketch: t functions (two-for-one) or 2t functions
     ordered (row 0 bucket, row 0 sign, row 1 bucket, ...) in two-poly mode."""
-    return draw_coeffs(b, c, k, t * (2 if mode == TWO_POLY else 1), seed)
+    return draw_coeffs(b, c, k, t * (2 if mode & TWO_POLY else 1), seed)
 
 
 def hash_eval(b: int, c: int, coeffs: np.ndarray, keys: np.ndarray) -> np.ndarray:
@@ -184,7 +185,7 @@ def f2_estimate(counters: np.ndarray) -> int:
 def cs_x_many(b: int, c: int, k: int, m: int, mode: int, coeffs: np.ndarray, keys: np.ndarray,
               weights=None) -> list:
     coeffs = np.ascontiguousarray(coeffs, dtype=np.uint64).reshape(-1, 2)
-    nf = 2 if mode == TWO_POLY else 1
+    nf = 2 if mode & TWO_POLY else 1
     nsets = coeffs.shape[0] // (nf * k)
     keys, kind, n = _keys(keys)
     if weights is not None:
@@ -254,7 +255,7 @@ def ints_to_limbs(vals, nlimbs: int) -> np.ndarray:
 def divmod_wide(b: int, c: int, v: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     """Quotient and remainder of wide values by p = 2^b - c, by definition
     (Python's integer floor division and remainder) -- the operation whose
-    fast form is Algorithm division-generalized + mod-generalized (Sec. 1.6;
+    fast form is Algorithm division-generalized + mod-generalized (Sec. 1.5;
     Table 2 of Sec. 5 times it for 2b-bit values).  v: (n, ceil(2b/64)) limbs;
     the value used is v mod 2^(2b).  Returns (q, r) as (n, ceil((b+1)/64)) and
     (n, ceil(b/64)) limb arrays."""

@@ -16,11 +16,11 @@
  *                  from SplitMix64 (Steele, Lea & Flood 2014).  The paper only
  *                  requires them uniform (Sec. 1.2); the draw order is this
  *                  project's convention.
- *  - or_cs_update: Count Sketch "Process" (Algorithm count-sketch, Sec. 1.4):
+ *  - or_cs_update: Count Sketch "Process" (Algorithm count-sketch, Sec. 1.3):
  *                  C[i(x)] += s(x) * Delta, one row of m counters per hash
  *                  function, t rows.  The bucket i(x) = h(x) mod m and the
  *                  sign bit a(x) = floor(h(x) / 2^(b-1)), s = 1 - 2a, are the
- *                  two-for-one split of Algorithm h-and-s (Sec. 1.4, "Two-for-
+ *                  two-for-one split of Algorithm h-and-s (Sec. 1.3, "Two-for-
  *                  one hash functions"), written with % and / rather than bit
  *                  masks.  In two-polynomial mode the sign bit comes from a
  *                  second, independent polynomial per row (Algorithm
@@ -30,10 +30,10 @@
  *                  the t rows (t odd) as the F2 estimate.
  *  - or_divmod:    floor(v / p) and v mod p for 128-bit v (what Algorithms
  *                  div-simple, division-generalized and mod-generalized of
- *                  Sec. 1.6 compute), by the C operators.
+ *                  Sec. 1.5 compute), by the C operators.
  *  - or_cs_point_query: the point-query estimate of f_x, median over rows of
- *                  s_r(x) C[r][i_r(x)] (Sec. 1.4, estimating a single value).
- *  - or_exact_f2:  F2 = sum_x f_x^2 of a weighted stream (Sec. 1.4 setup).
+ *                  s_r(x) C[r][i_r(x)] (Sec. 1.3, estimating a single value).
+ *  - or_exact_f2:  F2 = sum_x f_x^2 of a weighted stream (Sec. 1.3 setup).
  *
  * Conventions shared with the library's contract (not its code): counters are
  * int64 and wrap modulo 2^64; row sums of squares wrap modulo 2^128.
@@ -161,23 +161,49 @@ void or_hash_many(int b, u64 c, int k, const u64* coeff_pairs, u64 nfun, const u
 
 /* ---------------- Count Sketch ---------------- */
 
-/* Bucket and sign of one key in one row. */
-static void or_split(u128 p, int b, int k, u64 m, int two_poly, const u128* a_bucket,
+/* Bucket and sign of one key in one row.  mode bit 0 (two polynomials): the
+ * sign comes from the row's second polynomial.  mode bit 1 (any m): the
+ * bucket map for a number of buckets that need not be a power of two --
+ *   c = 1 (Mersenne, Algorithm Mersenne-arb-r of Sec. 3.3): h' = h + 1 is
+ *          nonzero in [2^b]; its low b-1 bits j give the bucket floor(j m /
+ *          2^(b-1)) and, in two-for-one mode, its top bit a the sign s = 2a - 1
+ *          (the sign convention of that section's text and proofs);
+ *   c > 1 (pseudo-Mersenne, Sec. 1.5 "arbitrary number of buckets"): the most
+ *          uniform map floor(h m / p); the sign then needs the second
+ *          polynomial (the library accepts this case only in that mode).
+ * Otherwise bucket = h mod m and the sign bit is floor(g / 2^(b-1)), s = 1 - 2a
+ * (Algorithm h-and-s).  Plain % and / throughout. */
+static void or_split(u128 p, int b, u64 c, int k, u64 m, int mode, const u128* a_bucket,
                      const u128* a_sign, u128 x, u64* bucket, int* sign) {
     u128 h = or_hash_p(p, k, a_bucket, x);
-    *bucket = (u64)(h % m);
-    u128 g = two_poly ? or_hash_p(p, k, a_sign, x) : h;
-    u128 bit = g / ((u128)1 << (b - 1));
+    u128 half = (u128)1 << (b - 1);
+    if (mode & 2) {
+        if (c == 1) {
+            u128 hx = h + 1;
+            u128 j = hx % half;
+            *bucket = (u64)((j * (u128)m) / half);
+            if (!(mode & 1)) {
+                *sign = 2 * (int)(hx / half) - 1;
+                return;
+            }
+        } else {
+            *bucket = (u64)((h * (u128)m) / p);
+        }
+    } else {
+        *bucket = (u64)(h % m);
+    }
+    u128 g = (mode & 1) ? or_hash_p(p, k, a_sign, x) : h;
+    u128 bit = g / half;
     *sign = 1 - 2 * (int)bit;
 }
 
 /* C (t x m, row-major int64) += sketch of the stream (keys, w); w == NULL means
  * unit weights.  coeffs: t*k pairs (two-for-one) or 2*t*k pairs ordered row 0
  * bucket function, row 0 sign function, row 1 bucket function, ... */
-void or_cs_update(int b, u64 c, int k, int t, u64 m, int two_poly, const u64* coeff_pairs,
+void or_cs_update(int b, u64 c, int k, int t, u64 m, int mode, const u64* coeff_pairs,
                   const void* keys, int key_kind, const int32_t* w, u64 n, int64_t* C) {
     u128 p = or_prime(b, c);
-    int nf = two_poly ? 2 : 1;
+    int nf = (mode & 1) ? 2 : 1;
     u128* a = (u128*)malloc(sizeof(u128) * (size_t)t * (size_t)nf * (size_t)k);
     for (int f = 0; f < t * nf; ++f) or_load_coeffs(coeff_pairs + 2 * (u64)f * (u64)k, k, a + f * k);
     for (u64 j = 0; j < n; ++j) {
@@ -185,10 +211,10 @@ void or_cs_update(int b, u64 c, int k, int t, u64 m, int two_poly, const u64* co
         int64_t wj = w ? (int64_t)w[j] : 1;
         for (int r = 0; r < t; ++r) {
             const u128* ab = a + (size_t)(r * nf) * k;
-            const u128* as = two_poly ? ab + k : ab;
+            const u128* as = (mode & 1) ? ab + k : ab;
             u64 bucket;
             int sign;
-            or_split(p, b, k, m, two_poly, ab, as, x, &bucket, &sign);
+            or_split(p, b, c, k, m, mode, ab, as, x, &bucket, &sign);
             u64* cell = (u64*)&C[(u64)r * m + bucket];
             *cell += (u64)(sign * wj); /* two's-complement add, wraps mod 2^64 */
         }
@@ -197,7 +223,7 @@ void or_cs_update(int b, u64 c, int k, int t, u64 m, int two_poly, const u64* co
 }
 
 typedef struct {
-    int b, k, t, two_poly, key_kind;
+    int b, k, t, mode, key_kind;
     u64 c, m, lo, hi;
     const u64* coeffs;
     const void* keys;
@@ -209,7 +235,7 @@ static void* or_chunk_main(void* arg) {
     or_chunk* ch = (or_chunk*)arg;
     const char* kbase = (const char*)ch->keys;
     size_t kb = ch->key_kind == 32 ? 4 : ch->key_kind == 64 ? 8 : 16;
-    or_cs_update(ch->b, ch->c, ch->k, ch->t, ch->m, ch->two_poly, ch->coeffs,
+    or_cs_update(ch->b, ch->c, ch->k, ch->t, ch->m, ch->mode, ch->coeffs,
                  kbase + kb * ch->lo, ch->key_kind, ch->w ? ch->w + ch->lo : NULL,
                  ch->hi - ch->lo, ch->C);
     return NULL;
@@ -217,12 +243,12 @@ static void* or_chunk_main(void* arg) {
 
 /* Same result as or_cs_update: the stream is cut into nthreads contiguous
  * pieces, each sketched into its own zeroed counters, and the counters are
- * summed (a Count Sketch is linear in the stream, Sec. 1.4). */
-void or_cs_update_mt(int b, u64 c, int k, int t, u64 m, int two_poly, const u64* coeff_pairs,
+ * summed (a Count Sketch is linear in the stream, Sec. 1.3). */
+void or_cs_update_mt(int b, u64 c, int k, int t, u64 m, int mode, const u64* coeff_pairs,
                      const void* keys, int key_kind, const int32_t* w, u64 n, int64_t* C,
                      int nthreads) {
     if (nthreads < 2 || n < 1024) {
-        or_cs_update(b, c, k, t, m, two_poly, coeff_pairs, keys, key_kind, w, n, C);
+        or_cs_update(b, c, k, t, m, mode, coeff_pairs, keys, key_kind, w, n, C);
         return;
     }
     if (nthreads > 256) nthreads = 256;
@@ -232,7 +258,7 @@ void or_cs_update_mt(int b, u64 c, int k, int t, u64 m, int two_poly, const u64*
     u64 cells = (u64)t * m;
     u64 per = (n + (u64)nthreads - 1) / (u64)nthreads;
     for (int i = 0; i < nthreads; ++i) {
-        ch[i] = (or_chunk){b, k, t, two_poly, key_kind, c, m, 0, 0, coeff_pairs, keys, w, NULL};
+        ch[i] = (or_chunk){b, k, t, mode, key_kind, c, m, 0, 0, coeff_pairs, keys, w, NULL};
         ch[i].lo = (u64)i * per < n ? (u64)i * per : n;
         ch[i].hi = ch[i].lo + per < n ? ch[i].lo + per : n;
         ch[i].C = (int64_t*)calloc(cells, sizeof(int64_t));
@@ -279,25 +305,25 @@ void or_cs_f2(int t, u64 m, const int64_t* C, u64* out_pair) {
 /* For each of nsets hash-function sets (1 function, or 2 in two-polynomial
  * mode), sketch the stream into ONE row of m counters and return that row's
  * X = sum C^2.  Used by the enumeration pins over all coefficient tuples. */
-void or_cs_x_many(int b, u64 c, int k, u64 m, int two_poly, const u64* coeff_pairs, u64 nsets,
+void or_cs_x_many(int b, u64 c, int k, u64 m, int mode, const u64* coeff_pairs, u64 nsets,
                   const void* keys, int key_kind, const int32_t* w, u64 n, u64* x_pairs) {
-    int nf = two_poly ? 2 : 1;
+    int nf = (mode & 1) ? 2 : 1;
     int64_t* C = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
     for (u64 s = 0; s < nsets; ++s) {
         memset(C, 0, sizeof(int64_t) * (size_t)m);
-        or_cs_update(b, c, k, 1, m, two_poly, coeff_pairs + 2 * s * (u64)(nf * k), keys, key_kind,
+        or_cs_update(b, c, k, 1, m, mode, coeff_pairs + 2 * s * (u64)(nf * k), keys, key_kind,
                      w, n, C);
         or_cs_row_sumsq(1, m, C, x_pairs + 2 * s);
     }
     free(C);
 }
 
-/* Point query (Sec. 1.4): the estimate of f_x is the median over the t rows of
+/* Point query (Sec. 1.3): the estimate of f_x is the median over the t rows of
  * s_r(x) * C[r][i_r(x)] (t odd: the middle value after sorting). */
-void or_cs_point_query(int b, u64 c, int k, int t, u64 m, int two_poly, const u64* coeff_pairs,
+void or_cs_point_query(int b, u64 c, int k, int t, u64 m, int mode, const u64* coeff_pairs,
                        const int64_t* C, const void* keys, int key_kind, u64 n, int64_t* out) {
     u128 p = or_prime(b, c);
-    int nf = two_poly ? 2 : 1;
+    int nf = (mode & 1) ? 2 : 1;
     u128* a = (u128*)malloc(sizeof(u128) * (size_t)t * (size_t)nf * (size_t)k);
     int64_t* est = (int64_t*)malloc(sizeof(int64_t) * (size_t)t);
     for (int f = 0; f < t * nf; ++f) or_load_coeffs(coeff_pairs + 2 * (u64)f * (u64)k, k, a + f * k);
@@ -305,10 +331,10 @@ void or_cs_point_query(int b, u64 c, int k, int t, u64 m, int two_poly, const u6
         u128 x = or_key(keys, key_kind, j);
         for (int r = 0; r < t; ++r) {
             const u128* ab = a + (size_t)(r * nf) * k;
-            const u128* as = two_poly ? ab + k : ab;
+            const u128* as = (mode & 1) ? ab + k : ab;
             u64 bucket;
             int sign;
-            or_split(p, b, k, m, two_poly, ab, as, x, &bucket, &sign);
+            or_split(p, b, c, k, m, mode, ab, as, x, &bucket, &sign);
             u64 cv = (u64)C[(u64)r * m + bucket];
             est[r] = (int64_t)(sign > 0 ? cv : (u64)0 - cv);
         }

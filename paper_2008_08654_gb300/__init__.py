@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libms.so")
 
 TWO_FOR_ONE = 0
 TWO_POLY = 1
+ANY_R = 2  # mode flag: any number of buckets m
 
 PLACE_SMEM, PLACE_DSMEM, PLACE_GLOBAL = 0, 1, 2
 STRAT_HORNER, STRAT_POWER_SUM = 0, 1
@@ -77,6 +78,7 @@ def _load():
         "cs_create_coeffs": (i, [pp, i, u32, i, i, u64, i, vp]),
         "cs_destroy": (i, [vp]),
         "cs_params": (i, [vp, ip, ctypes.POINTER(u32), ip, ip, ctypes.POINTER(u64), ip]),
+        "cs_row_stride": (i, [vp, ctypes.POINTER(u32)]),
         "cs_coeffs": (i, [vp, vp]),
         "cs_update": (i, [vp, vp, vp, sz, vp]),
         "cs_estimate_f2": (i, [vp, vp, vp, vp]),
@@ -296,13 +298,16 @@ class Sketch:
                               ctypes.byref(bb), ctypes.byref(cc), ctypes.byref(md)), "cs_params")
         self.t, self.m, self.k, self.b, self.c, self.mode = (tt.value, mm.value, kk.value,
                                                              bb.value, cc.value, md.value)
+        st = ctypes.c_uint32()
+        _check(lib_.cs_row_stride(h, ctypes.byref(st)), "cs_row_stride")
+        self.stride = st.value  # counters per row in memory (> m only for ANY_R sketches)
 
     @property
     def handle(self):
         return self._h
 
     def coeffs(self) -> list:
-        n = self.t * self.k * (2 if self.mode == TWO_POLY else 1)
+        n = self.t * self.k * (2 if self.mode & TWO_POLY else 1)
         arr = (U128 * n)()
         _check(_load().cs_coeffs(self._h, arr), "cs_coeffs")
         return [a.lo | (a.hi << 64) for a in arr]
@@ -343,11 +348,14 @@ class Sketch:
                "cs_point_query")
         return out
 
-    def counters(self) -> torch.Tensor:
-        """Zero-copy (t, m) int64 view of the library-owned counters."""
+    def counters(self, padded: bool = False) -> torch.Tensor:
+        """Zero-copy (t, m) int64 view of the library-owned counters (rows are
+        `stride` apart in memory; padded=True returns the full (t, stride))."""
         p = ctypes.c_void_p()
         _check(_load().cs_counters(self._h, ctypes.byref(p)), "cs_counters")
-        return torch.as_tensor(_CudaView(p.value, (self.t, self.m), "<i8", self), device="cuda")
+        full = torch.as_tensor(_CudaView(p.value, (self.t, self.stride), "<i8", self),
+                               device="cuda")
+        return full if padded or self.stride == self.m else full[:, :self.m]
 
     def reset(self, stream=None):
         _check(_load().cs_reset(self._h, _stream(stream)), "cs_reset")

@@ -1,5 +1,5 @@
 // Quotient and remainder of wide values by p = 2^b - c (b up to 1024):
-// Algorithm division-generalized (Sec. 1.6; step count from the theorem of
+// Algorithm division-generalized (Sec. 1.5; step count from the theorem of
 // Sec. 4), then Algorithm mod-generalized.
 //
 // Layout on the GPU: a warp is cut into segments of S lanes (S a power of two,

@@ -124,7 +124,7 @@ cudaError_t query_cs_update_occupancy(int prime, const UpdateArgs& a, const u64*
 
 // ================================================================ point query
 //
-// X_x = s(x) C[i(x)] per row, and the median over rows (Sec. 1.4, the
+// X_x = s(x) C[i(x)] per row, and the median over rows (Sec. 1.3, the
 // point-query use of the Count Sketch).  Runtime t and k; coefficients are
 // staged in shared memory.
 template <class F, int MODE>
@@ -158,8 +158,10 @@ __global__ void __launch_bounds__(256) k_cs_point_query(const QueryArgs a) {
                     z = Ops::mul_add(z, x, coef_at<F, 0, 0>(dummy, scoef, true, a.k, fb + 1, i));
                 g = Ops::canon(z);
             }
-            const long long cval = a.counters[((u64)r << a.log2m) + Ops::bucket(h, mask)];
-            est[r] = Ops::sign_bit(g) ? -cval : cval;
+            u32 bucket, sb;
+            split_row<F, NF>(h, g, mask, a.arb_r, bucket, sb);
+            const long long cval = a.counters[((u64)r << a.log2m) + bucket];
+            est[r] = sb ? -cval : cval;
         }
         for (int i = 1; i < a.t; ++i) {
             const long long v = est[i];
@@ -344,7 +346,7 @@ cudaError_t launch_hash_eval(int prime, const void* keys, void* out, u64 n, int 
 
 // ================================================================ division
 //
-// Algorithm division-generalized (Sec. 1.6) on a 129-bit running value: the
+// Algorithm division-generalized (Sec. 1.5) on a 129-bit running value: the
 // input v < 2^128 plus c can carry into bit 128, so (value, carry) pairs are
 // kept and shifted together.  STEPS covers all of [0, 2^128) by the theorem
 // of Sec. 4.  Algorithm mod-generalized then gives the remainder from the low

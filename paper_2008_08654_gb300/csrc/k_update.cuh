@@ -1,4 +1,4 @@
-// Count Sketch update kernel (Algorithm count-sketch "Process", Sec. 1.4) and
+// Count Sketch update kernel (Algorithm count-sketch "Process", Sec. 1.3) and
 // the per-prime hashing glue it needs.  Included by one translation unit per
 // prime, which instantiates the launch dispatcher for that prime.
 //
@@ -57,6 +57,9 @@ struct FieldOps<msf::P61> {
     __device__ static __forceinline__ val_t from_words(const u64* w) { return w[0]; }
     __device__ static __forceinline__ u32 bucket(val_t h, u32 mask) { return F::bucket(h, mask); }
     __device__ static __forceinline__ u32 sign_bit(val_t h) { return F::sign_bit(h); }
+    __device__ static __forceinline__ void arb_split(val_t h, u32 r, u32& bucket, u32& a) {
+        F::arb_split(h, r, bucket, a);
+    }
 };
 
 template <>
@@ -74,6 +77,9 @@ struct FieldOps<msf::P31> {
     __device__ static __forceinline__ val_t from_words(const u64* w) { return (u32)w[0]; }
     __device__ static __forceinline__ u32 bucket(val_t h, u32 mask) { return F::bucket(h, mask); }
     __device__ static __forceinline__ u32 sign_bit(val_t h) { return F::sign_bit(h); }
+    __device__ static __forceinline__ void arb_split(val_t h, u32 r, u32& bucket, u32& a) {
+        F::arb_split(h, r, bucket, a);
+    }
 };
 
 template <>
@@ -91,6 +97,9 @@ struct FieldOps<msf::P64> {
     __device__ static __forceinline__ val_t from_words(const u64* w) { return w[0]; }
     __device__ static __forceinline__ u32 bucket(val_t h, u32 mask) { return F::bucket(h, mask); }
     __device__ static __forceinline__ u32 sign_bit(val_t h) { return F::sign_bit(h); }
+    __device__ static __forceinline__ void arb_split(val_t h, u32 r, u32& bucket, u32& a) {
+        F::arb_split(h, r, bucket, a);
+    }
 };
 
 template <>
@@ -112,7 +121,31 @@ struct FieldOps<msf::P89> {
     }
     __device__ static __forceinline__ u32 bucket(val_t h, u32 mask) { return F::bucket(h, mask); }
     __device__ static __forceinline__ u32 sign_bit(val_t h) { return F::sign_bit(h); }
+    __device__ static __forceinline__ void arb_split(val_t h, u32 r, u32& bucket, u32& a) {
+        F::arb_split(h, r, bucket, a);
+    }
 };
+
+// Bucket and sign flag (1: the update is subtracted) of one row from its hash
+// value(s).  arb_r == 0: Algorithm h-and-s (the low bits of h and its bit
+// b-1).  arb_r > 0, any number of buckets: Algorithm Mersenne-arb-r for c = 1,
+// whose two-for-one sign is s = 2a - 1 from the same h + 1 (Sec. 3.3), or
+// floor(h r / p) for 2^64 - 59; with two polynomials the sign is always bit
+// b-1 of the second one.
+template <class F, int NF>
+__device__ __forceinline__ void split_row(const typename FieldOps<F>::val_t& h,
+                                          const typename FieldOps<F>::val_t& g, u32 mask,
+                                          u32 arb_r, u32& bucket, u32& sign) {
+    typedef FieldOps<F> Ops;
+    if (arb_r) {
+        u32 a;
+        Ops::arb_split(h, arb_r, bucket, a);
+        sign = (NF == 2) ? Ops::sign_bit(g) : (a ^ 1u);
+    } else {
+        bucket = Ops::bucket(h, mask);
+        sign = Ops::sign_bit(g);
+    }
+}
 
 // ------------------------------------------------------------ coefficients
 //
@@ -377,7 +410,7 @@ __device__ __forceinline__ void p61_row_bs(const msf::P61::Pow3& xp, const PC& p
 template <class F, int NF>
 __device__ __forceinline__ void update_big_key(const typename FieldOps<F>::Prep& xq, int w,
                                                const u64* coef, int t, int k, int log2m,
-                                               long long* counters) {
+                                               u32 arb_r, long long* counters) {
     typedef FieldOps<F> Ops;
     typedef typename Ops::val_t val_t;
     constexpr int W = Ops::WORDS;
@@ -397,8 +430,9 @@ __device__ __forceinline__ void update_big_key(const typename FieldOps<F>::Prep&
             for (int i = k - 2; i >= 0; --i) z = Ops::mul_add(z, xq, Ops::from_words(cs + (size_t)i * W));
             g = Ops::canon(z);
         }
-        const long long d = Ops::sign_bit(g) ? -(long long)w : (long long)w;
-        global_add64(counters + ((u64)r << log2m) + Ops::bucket(h, mask), d);
+        u32 bucket, sb;
+        split_row<F, NF>(h, g, mask, arb_r, bucket, sb);
+        global_add64(counters + ((u64)r << log2m) + bucket, sb ? -(long long)w : (long long)w);
     }
 }
 
@@ -509,7 +543,7 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
             for (int q = 0; q < 4; ++q) {
                 if (big[q]) {
                     update_big_key<F, NF>(Ops::prep(key[q]), wt[q], a.coef_dev, t, k, log2m,
-                                          a.counters);
+                                          a.arb_r, a.counters);
                     wt[q] = 0;
                 }
             }
@@ -576,9 +610,12 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    if (wt[q] != 0)
-                        apply_update<PLACE>(tile, tile_saddr, a.counters, r, Ops::bucket(h[q], mask),
-                                            Ops::sign_bit(g[q]), wt[q], big[q], m, log2m, lcs);
+                    if (wt[q] != 0) {
+                        u32 bucket, sb;
+                        split_row<F, NF>(h[q], g[q], mask, a.arb_r, bucket, sb);
+                        apply_update<PLACE>(tile, tile_saddr, a.counters, r, bucket, sb, wt[q],
+                                            big[q], m, log2m, lcs);
+                    }
                 }
             }
         }
@@ -605,8 +642,10 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                                 z = Ops::mul_add(z, xq, MSK_COEF(fb + 1, i2));
                             g = Ops::canon(z);
                         }
-                        apply_update<PLACE>(tile, tile_saddr, a.counters, r, Ops::bucket(h, mask),
-                                            Ops::sign_bit(g), cnt, false, m, log2m, lcs);
+                        u32 bucket, sb;
+                        split_row<F, NF>(h, g, mask, a.arb_r, bucket, sb);
+                        apply_update<PLACE>(tile, tile_saddr, a.counters, r, bucket, sb, cnt, false,
+                                            m, log2m, lcs);
                     }
                 }
             }

@@ -38,6 +38,12 @@ static cudaError_t launch_exact(const UpdateArgs& a, const u64* coef_host, const
     constexpr int NF = (MODE == CS_TWO_POLY) ? 2 : 1;
     auto kern = k_cs_update<F, T, K, MODE, PLACE, STRAT>;
     cudaError_t e;
+    if (T == 0) {  // the generic kernel stages the coefficients after the tile
+        const size_t tile = PLACE == PLACE_GLOBAL ? 0
+                            : ((size_t)a.t << a.log2m) * 4 / (size_t)(cfg.cluster > 0 ? cfg.cluster : 1);
+        const size_t coef = (size_t)a.t * NF * a.k * FieldOps<F>::WORDS * 8;
+        if (cfg.smem < tile + coef) return cudaErrorInvalidValue;
+    }
     if (cfg.smem > 48 * 1024) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
         if (e != cudaSuccess) return e;
@@ -108,13 +114,10 @@ static cudaError_t launch_mode(const UpdateArgs& a, const u64* coef_host, const 
 template <class F>
 cudaError_t launch_update_for(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
                               cudaStream_t stream, int* specialized, int* occupancy) {
-    if (a.k == 4 && a.t == 5) {
+    if (update_is_specialized(a.t, a.k, a.arb_r)) {
         if (specialized) *specialized = 1;
-        return launch_mode<F, 5, 4>(a, coef_host, cfg, stream, occupancy);
-    }
-    if (a.k == 4 && a.t == 7) {
-        if (specialized) *specialized = 1;
-        return launch_mode<F, 7, 4>(a, coef_host, cfg, stream, occupancy);
+        return a.t == 5 ? launch_mode<F, 5, 4>(a, coef_host, cfg, stream, occupancy)
+                        : launch_mode<F, 7, 4>(a, coef_host, cfg, stream, occupancy);
     }
     if (specialized) *specialized = 0;
     return launch_mode<F, 0, 0>(a, coef_host, cfg, stream, occupancy);

@@ -79,7 +79,8 @@ extern "C" ms_status cs_batch_create(cs_batch** out, const cs_batch_job* jobs_ho
     for (int j = 0; j < count; ++j) {
         const cs_batch_job& jb = jobs_host[j];
         const cs_sketch* sk = jb.sketch;
-        if (!sk || sk->prime != s0->prime || sk->k != s0->k || sk->mode != s0->mode)
+        if (!sk || sk->prime != s0->prime || sk->k != s0->k || sk->mode != s0->mode ||
+            sk->r != 0)  // power-of-two bucket counts only
             return MS_ERR_INVALID_ARG;
         if (jb.n > 0 && !jb.keys_dev) return MS_ERR_INVALID_ARG;
         const size_t kb = msi::key_bytes(sk->prime);

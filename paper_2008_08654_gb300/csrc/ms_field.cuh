@@ -6,13 +6,13 @@
 //   Horner / power-sum building blocks with LAZY reduction: intermediate
 //                     values stay below 2^b + 2^4 (not necessarily < p), and
 //                     only the final value is made canonical,
-//   bucket(h, mask)   the low bits of h (Algorithm h-and-s, Sec. 1.4),
+//   bucket(h, mask)   the low bits of h (Algorithm h-and-s, Sec. 1.3),
 //   sign_bit(h)       bit b-1 of h (the same algorithm).
 //
 // Mersenne reduction uses the fold y = (y mod 2^b) + floor(y / 2^b), which
 // preserves y mod p because 2^b = 1 (mod p) (eq. Mersenne, Sec. 1.2).  The
 // pseudo-Mersenne prime 2^64 - 59 uses Algorithm division-generalized and
-// Algorithm mod-generalized (Sec. 1.6) with 3 steps.
+// Algorithm mod-generalized (Sec. 1.5) with 3 steps.
 //
 // Every bound below is for the stated input ranges; the comments give the
 // arithmetic so that each can be checked by hand.
@@ -89,6 +89,16 @@ struct P61 {
 
     __device__ static __forceinline__ u32 bucket(u64 h, u32 mask) { return (u32)h & mask; }
     __device__ static __forceinline__ u32 sign_bit(u64 h) { return (u32)(h >> 60) & 1u; }
+
+    // Algorithm Mersenne-arb-r (Sec. 3.3) for a canonical h < p and r buckets:
+    // h' = h + 1 is nonzero in [2^61]; the bucket is floor(r j / 2^60) for its
+    // low 60 bits j (a most uniform map, Lemma most-uniform), a its top bit.
+    __device__ static __forceinline__ void arb_split(u64 h, u32 r, u32& bucket, u32& a) {
+        const u64 hx = h + 1;
+        const u64 j = hx & ((1ull << 60) - 1);
+        bucket = (u32)((__umul64hi(j, (u64)r) << 4) | ((j * (u64)r) >> 60));
+        a = (u32)(hx >> 60);
+    }
 
     // 32x32 -> 64-bit multiply-add, a * b + c (one wide integer multiply-add).
     __device__ static __forceinline__ u64 madw(u32 a, u32 b, u64 c) {
@@ -242,6 +252,14 @@ struct P31 {
 
     __device__ static __forceinline__ u32 bucket(u32 h, u32 mask) { return h & mask; }
     __device__ static __forceinline__ u32 sign_bit(u32 h) { return (h >> 30) & 1u; }
+
+    // Algorithm Mersenne-arb-r (Sec. 3.3): h' = h + 1, bucket floor(r j / 2^30)
+    // for its low 30 bits j, a = its top bit.
+    __device__ static __forceinline__ void arb_split(u32 h, u32 r, u32& bucket, u32& a) {
+        const u32 hx = h + 1u;
+        bucket = (u32)(((u64)(hx & 0x3FFFFFFFu) * r) >> 30);
+        a = hx >> 30;
+    }
 };
 
 // ---------------------------------------------------------------- p = 2^89-1
@@ -291,6 +309,15 @@ struct P89 {
 
     __device__ static __forceinline__ u32 bucket(u128 h, u32 mask) { return (u32)h & mask; }
     __device__ static __forceinline__ u32 sign_bit(u128 h) { return (u32)(h >> 88) & 1u; }
+
+    // Algorithm Mersenne-arb-r (Sec. 3.3): h' = h + 1, bucket floor(r j / 2^88)
+    // for its low 88 bits j (r j < 2^120), a = its top bit.
+    __device__ static __forceinline__ void arb_split(u128 h, u32 r, u32& bucket, u32& a) {
+        const u128 hx = h + 1;
+        const u128 j = hx & ((((u128)1) << 88) - 1);
+        bucket = (u32)((j * (u128)r) >> 88);
+        a = (u32)(hx >> 88);
+    }
 };
 
 // ------------------------------------------------------------ p = 2^64-59
@@ -312,12 +339,25 @@ struct P64 {
     //   v' = v + c < 2^128 (no carry out: (p-1)p + c < 2^128 - 2^70)
     //   z  = v' >> 64;  z = (z c + v') >> 64  (twice)   -> floor(v / p) < 2^64
     //   y  = (v + z c) mod 2^64                          -> v mod p
-    __device__ static __forceinline__ u64 mod_p(u128 v) {
+    __device__ static __forceinline__ u64 mod_p(u128 v) { return (u64)v + div_p(v) * C; }
+
+    // floor(v / p) for the same v (the three division steps above).
+    __device__ static __forceinline__ u64 div_p(u128 v) {
         const u128 vp = v + C;
         u64 z = (u64)(vp >> 64);
         z = (u64)(((u128)z * C + vp) >> 64);
         z = (u64)(((u128)z * C + vp) >> 64);
-        return (u64)v + z * C;
+        return z;
+    }
+
+    // Any number r of buckets for a pseudo-Mersenne prime: the most uniform map
+    // floor(h r / p) (Sec. 1.5, "Applications to an arbitrary number of
+    // buckets"), by Algorithm division-generalized.  h r < 2^96 is in range.
+    // There is no sign bit to pair with it; sketches take the sign from a
+    // second polynomial.
+    __device__ static __forceinline__ void arb_split(u64 h, u32 r, u32& bucket, u32& a) {
+        bucket = (u32)div_p((u128)h * r);
+        a = 0;
     }
 
     __device__ static __forceinline__ u64 mul_add(u64 z, u64 x, u64 a) {

@@ -332,20 +332,30 @@ static void sketch_free_device(cs_sketch* sk) {
     sk->block = nullptr;
 }
 
-static ms_status sketch_make(cs_sketch** out, int t, uint32_t m, int k, int b, uint64_t c, int mode,
-                             const u64* words) {
+static uint32_t next_pow2(uint32_t m) {
+    uint32_t s = 1;
+    while (s < m) s <<= 1;
+    return s;
+}
+
+// m_req: the number of buckets as created (any value for CS_ANY_R); the rows
+// are stored m = m_req wide, or 2^ceil(log2 m_req) wide for CS_ANY_R.
+static ms_status sketch_make(cs_sketch** out, int t, uint32_t m_req, int k, int b, uint64_t c,
+                             int mode, const u64* words) {
     const int prime = prime_id(b, c);
     cs_sketch* sk = new (std::nothrow) cs_sketch;
     if (!sk) return MS_ERR_OOM;
     sk->t = t;
-    sk->m = m;
-    sk->log2m = ilog2_exact(m);
+    sk->r = (mode & CS_ANY_R) ? m_req : 0u;
+    sk->m = (mode & CS_ANY_R) ? next_pow2(m_req) : m_req;
+    sk->log2m = ilog2_exact(sk->m);
+    const uint32_t m = sk->m;  // every size below is in rows of the storage width
     sk->k = k;
     sk->b = b;
     sk->c = c;
     sk->mode = mode;
     sk->prime = prime;
-    const int nf = mode == CS_TWO_POLY ? 2 : 1;
+    const int nf = (mode & CS_TWO_POLY) ? 2 : 1;
     const size_t nwords = (size_t)t * nf * k * words_per_value(prime);
     sk->words.assign(words, words + nwords);
     sk->f2_splits = 1;
@@ -400,7 +410,13 @@ static ms_status validate_sketch_params(int t, uint32_t m, int k, int b, uint64_
     if (prime_id(b, c) < 0) return MS_ERR_UNSUPPORTED_PRIME;
     if (t < 1 || t > msk::MAX_T || (t % 2) == 0) return MS_ERR_INVALID_ARG;
     if (k < 1 || k > msk::MAX_K) return MS_ERR_INVALID_ARG;
-    if (mode != CS_TWO_FOR_ONE && mode != CS_TWO_POLY) return MS_ERR_INVALID_ARG;
+    if ((mode & ~(CS_TWO_POLY | CS_ANY_R)) != 0) return MS_ERR_INVALID_ARG;
+    if (mode & CS_ANY_R) {
+        if (m < 2 || m > (1u << 24) || (uint64_t)m > (1ull << (b - 2))) return MS_ERR_INVALID_ARG;
+        // floor(h m / p) has no sign bit to pair with (pseudo-Mersenne)
+        if (c != 1 && !(mode & CS_TWO_POLY)) return MS_ERR_INVALID_ARG;
+        return MS_OK;
+    }
     const int l = ilog2_exact(m);
     if (l < 1 || l > 24 || l >= b - 1) return MS_ERR_INVALID_ARG;
     return MS_OK;
@@ -412,7 +428,7 @@ extern "C" ms_status cs_create(cs_sketch** out, int t, uint32_t m, int k, int b,
     *out = nullptr;
     ms_status st = validate_sketch_params(t, m, k, b, c, mode);
     if (st != MS_OK) return st;
-    const int nf = mode == CS_TWO_POLY ? 2 : 1;
+    const int nf = (mode & CS_TWO_POLY) ? 2 : 1;
     const int W = words_per_value(prime_id(b, c));
     std::vector<u64> w((size_t)t * nf * k * W);
     draw_uniform_below_p(b, c, seed, t * nf * k, w.data());
@@ -426,7 +442,7 @@ extern "C" ms_status cs_create_coeffs(cs_sketch** out, int t, uint32_t m, int k,
     if (!coeffs_host) return MS_ERR_INVALID_ARG;
     ms_status st = validate_sketch_params(t, m, k, b, c, mode);
     if (st != MS_OK) return st;
-    const int nf = mode == CS_TWO_POLY ? 2 : 1;
+    const int nf = (mode & CS_TWO_POLY) ? 2 : 1;
     const int W = words_per_value(prime_id(b, c));
     const int nv = t * nf * k;
     std::vector<u64> w((size_t)nv * W);
@@ -449,11 +465,17 @@ extern "C" ms_status cs_params(const cs_sketch* sk, int* t, uint32_t* m, int* k,
                                uint64_t* c, int* mode) {
     if (!sk) return MS_ERR_INVALID_ARG;
     if (t) *t = sk->t;
-    if (m) *m = sk->m;
+    if (m) *m = sk->r ? sk->r : sk->m;
     if (k) *k = sk->k;
     if (b) *b = sk->b;
     if (c) *c = sk->c;
     if (mode) *mode = sk->mode;
+    return MS_OK;
+}
+
+extern "C" ms_status cs_row_stride(const cs_sketch* sk, uint32_t* stride) {
+    if (!sk || !stride) return MS_ERR_INVALID_ARG;
+    *stride = sk->m;
     return MS_OK;
 }
 
@@ -474,9 +496,9 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
     const DevInfo d = device_info();
     if (!d.ok) return cuda_fail(cudaGetLastError(), "device query");
     const LaunchOverride& ov = sk->launch;
-    const int nf = sk->mode == CS_TWO_POLY ? 2 : 1;
+    const int nf = (sk->mode & CS_TWO_POLY) ? 2 : 1;
     const size_t coef_bytes = (size_t)sk->t * nf * sk->k * words_per_value(sk->prime) * 8;
-    const bool generic = !(sk->k == 4 && (sk->t == 5 || sk->t == 7));
+    const bool generic = !msk::update_is_specialized(sk->t, sk->k, sk->r);
     const size_t extra = generic ? (coef_bytes + 15) / 16 * 16 : 0;
     const size_t tile_bytes = (size_t)sk->t * sk->m * 4;
     const size_t optin = (size_t)d.smem_optin;
@@ -520,7 +542,8 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
     a.t = sk->t;
     a.k = sk->k;
     a.log2m = sk->log2m;
-    a.mode = sk->mode;
+    a.mode = sk->mode & CS_TWO_POLY;
+    a.arb_r = sk->r;
     a.cluster_log2 = lcs;
     a.coef_dev = sk->coef_dev;
     a.counters = sk->counters;
@@ -664,7 +687,8 @@ extern "C" ms_status cs_point_query(const cs_sketch* sk, const void* keys_dev, i
     a.t = sk->t;
     a.k = sk->k;
     a.log2m = sk->log2m;
-    a.mode = sk->mode;
+    a.mode = sk->mode & CS_TWO_POLY;
+    a.arb_r = sk->r;
     a.out = (long long*)out_dev;
     MS_CUDA(msk::launch_cs_point_query(sk->prime, a, (cudaStream_t)stream), "cs_point_query");
     return MS_OK;
@@ -684,8 +708,8 @@ extern "C" ms_status cs_reset(cs_sketch* sk, void* stream) {
 
 extern "C" ms_status cs_merge(cs_sketch* dst, const cs_sketch* src, void* stream) {
     if (!dst || !src) return MS_ERR_INVALID_ARG;
-    if (dst->t != src->t || dst->m != src->m || dst->k != src->k || dst->prime != src->prime ||
-        dst->mode != src->mode || dst->words != src->words)
+    if (dst->t != src->t || dst->m != src->m || dst->r != src->r || dst->k != src->k ||
+        dst->prime != src->prime || dst->mode != src->mode || dst->words != src->words)
         return MS_ERR_INVALID_ARG;
     if (dst == src) return MS_ERR_INVALID_ARG;
     MS_CUDA(msk::launch_add_counters(dst->counters, src->counters, (u64)dst->t * dst->m,
@@ -725,7 +749,7 @@ extern "C" ms_status cs_export(const cs_sketch* sk, void* buf_host, size_t* size
     memcpy(h.magic, kMagic, 8);
     h.version = 1;
     h.t = sk->t;
-    h.m = sk->m;
+    h.m = sk->r ? sk->r : sk->m;  // as created; the counters follow in rows of sk->m
     h.k = sk->k;
     h.b = sk->b;
     h.mode = sk->mode;
@@ -750,10 +774,11 @@ extern "C" ms_status cs_import(cs_sketch** out, const void* buf_host, size_t siz
     if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return MS_ERR_INVALID_ARG;
     ms_status st = validate_sketch_params(h.t, h.m, h.k, h.b, h.c, h.mode);
     if (st != MS_OK) return st;
-    const int nf = h.mode == CS_TWO_POLY ? 2 : 1;
+    const int nf = (h.mode & CS_TWO_POLY) ? 2 : 1;
     const int W = words_per_value(prime_id(h.b, h.c));
     if (h.nwords != (uint64_t)h.t * nf * h.k * W) return MS_ERR_INVALID_ARG;
-    const size_t need = sizeof(h) + h.nwords * 8 + (size_t)h.t * h.m * 8;
+    const uint32_t stride = (h.mode & CS_ANY_R) ? next_pow2(h.m) : h.m;
+    const size_t need = sizeof(h) + h.nwords * 8 + (size_t)h.t * stride * 8;
     if (size < need) return MS_ERR_INVALID_ARG;
     const u64* words = (const u64*)((const char*)buf_host + sizeof(h));
     for (uint64_t i = 0; i < h.nwords / W; ++i)
@@ -763,7 +788,7 @@ extern "C" ms_status cs_import(cs_sketch** out, const void* buf_host, size_t siz
     st = sketch_make(&sk, h.t, h.m, h.k, h.b, h.c, h.mode, words);
     if (st != MS_OK) return st;
     cudaError_t e = cudaMemcpy(sk->counters, (const char*)buf_host + sizeof(h) + h.nwords * 8,
-                               (size_t)h.t * h.m * 8, cudaMemcpyHostToDevice);
+                               (size_t)h.t * stride * 8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cs_destroy(sk);
         return cuda_fail(e, "cs_import");

@@ -22,7 +22,8 @@ struct LaunchOverride {
 
 struct cs_sketch {
     int t, k, b, mode, prime, log2m;
-    uint32_t m;
+    uint32_t m;                   // counters per row in memory (a power of two)
+    uint32_t r = 0;               // CS_ANY_R: the number of buckets (<= m); 0 otherwise
     uint64_t c;
     std::vector<msk::u64> words;  // host copy of the coefficients (limbs)
     void* block = nullptr;        // single device allocation holding everything below

@@ -48,7 +48,17 @@ struct UpdateArgs {
     int aggregate;           // PLACE_GLOBAL, unit weights: merge equal keys of a warp
     int hot_log2;            // PLACE_GLOBAL, unit weights: log2 slots of the per-block
                              // hot-key table in shared memory (0 = none)
+    u32 arb_r;               // any number of buckets: r (rows are 2^log2m >= r wide);
+                             // 0: power-of-two buckets (generic kernels only)
 };
+
+// Whether cs_update runs a compile-time (t, k) kernel (coefficients in the
+// parameter space) or the generic one (coefficients staged in shared memory
+// after the counter tile, which the launch's shared memory must cover).  The
+// host's launch choice and the dispatcher both ask this one function.
+inline bool update_is_specialized(int t, int k, u32 arb_r) {
+    return arb_r == 0 && k == 4 && (t == 5 || t == 7);
+}
 
 // Launch configuration chosen on the host.
 struct LaunchCfg {
@@ -100,6 +110,7 @@ struct QueryArgs {
     const long long* counters;
     const u64* coef_dev;
     int t, k, log2m, mode;
+    u32 arb_r;  // as in UpdateArgs
     long long* out;
 };
 cudaError_t launch_cs_point_query(int prime, const QueryArgs& a, cudaStream_t stream);

@@ -336,6 +336,7 @@ ms_status submit(ms_server* s, Req r, int try_only, uint64_t* ticket) {
 extern "C" ms_status ms_server_create(ms_server** out, const ms_server_config* cfg) {
     if (!out || !cfg) return MS_ERR_INVALID_ARG;
     *out = nullptr;
+    if ((cfg->mode & ~CS_TWO_POLY) != 0) return MS_ERR_INVALID_ARG;  // no CS_ANY_R here
     if (cfg->num_sketches < 1 || !cfg->m_per_sketch || cfg->staging_bytes < 4096 ||
         cfg->max_inflight < 1 || cfg->max_batch_requests < 1 || cfg->max_batch_keys < 1 ||
         cfg->timeout_s <= 0)

@@ -1,6 +1,6 @@
 """Multi-GPU form of the Count Sketch: shard the stream, merge by one sum.
 
-A Count Sketch is linear in its stream (Sec. 1.4), so ranks that sketch
+A Count Sketch is linear in its stream (Sec. 1.3), so ranks that sketch
 disjoint pieces of one stream with the SAME coefficients (same seed) hold
 partial sketches whose element-wise int64 sum is the sketch of the whole
 stream.  merge_counters_() performs that single exchange -- an all-reduce of

@@ -102,7 +102,12 @@ def test_invalid_arguments_are_rejected_on_the_host(ms):
         ((5, 1 << 20, 4, 31, 1, 0, 0), 0),  # allowed: 2^20 < 2^30
         ((5, 1024, 0, 61, 1, 0, 0), 1),     # k = 0
         ((5, 1024, 9, 61, 1, 0, 0), 1),     # k = 9
-        ((5, 1024, 4, 61, 1, 0, 2), 1),     # bad mode
+        ((5, 1024, 4, 61, 1, 0, 4), 1),     # bad mode
+        ((5, 1024, 4, 61, 1, 0, 6), 1),     # bad mode bits with CS_ANY_R
+        ((5, 1000, 4, 64, 59, 0, 2), 1),    # any m at 2^64-59 needs two polynomials
+        ((5, 1, 4, 61, 1, 0, 2), 1),        # any m: m too small
+        ((5, (1 << 24) + 1, 4, 61, 1, 0, 2), 1),  # any m: m too large
+        ((5, (1 << 29) + 1, 4, 31, 1, 0, 2), 1),  # any m: m > 2^(b-2)
         ((5, 1024, 4, 62, 1, 0, 0), 2),     # unsupported prime
         ((5, 1024, 4, 64, 1, 0, 0), 2),
         ((5, 1024, 4, 61, 3, 0, 0), 2),
@@ -118,6 +123,11 @@ def test_invalid_arguments_are_rejected_on_the_host(ms):
     assert lib.ms_div(62, 1, None, None, None, 5, None) == 2
     assert lib.ms_div(61, 1, None, None, None, 0, None) == 0   # n == 0: no-op
     assert lib.ms_mod(61, 1, None, None, 3, None) == 1
+    assert lib.ms_div_wide(31, 1, None, None, None, 5, None) == 1     # b < 32
+    assert lib.ms_div_wide(1025, 1, None, None, None, 5, None) == 1   # b > 1024
+    assert lib.ms_div_wide(64, 1 << 32, None, None, None, 5, None) == 1
+    assert lib.ms_div_wide(128, 1, None, None, None, 0, None) == 0    # n == 0: no-op
+    assert lib.ms_div_wide(128, 1, None, None, None, 5, None) == 1    # null buffers
     assert lib.cs_update(None, None, None, 10, None) == 1
     assert lib.cs_estimate_f2(None, None, None, None) == 1
     assert lib.cs_merge(None, None, None) == 1

@@ -53,7 +53,7 @@ def test_divmod_wide_ignores_bits_above_2b():
 
 
 def _paper_division(v, b, c, steps):
-    """Algorithm division-generalized (Sec. 1.6) on Python integers."""
+    """Algorithm division-generalized (Sec. 1.5) on Python integers."""
     vp = v + c
     z = vp >> b
     for _ in range(steps - 1):

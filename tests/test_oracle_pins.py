@@ -89,7 +89,7 @@ def test_divmod_matches_bigint(b, c):
 
 
 def _paper_division(v, b, c, steps):
-    """Algorithm division-generalized (Sec. 1.6) restated on Python integers:
+    """Algorithm division-generalized (Sec. 1.5) restated on Python integers:
     v' = v + c; z = v' >> b; then steps-1 times z = (z*c + v') >> b."""
     vp = v + c
     z = vp >> b
@@ -99,7 +99,7 @@ def _paper_division(v, b, c, steps):
 
 
 def _paper_mod(v, z, b, c):
-    """Algorithm mod-generalized (Sec. 1.6): y = (v + z*c) & (2^b - 1)."""
+    """Algorithm mod-generalized (Sec. 1.5): y = (v + z*c) & (2^b - 1)."""
     return (v + z * c) & ((1 << b) - 1)
 
 
@@ -367,7 +367,7 @@ def test_sign_bit_is_top_bit():
 
 
 def test_linearity_and_threads():
-    """Count Sketch is linear (Sec. 1.4): sketch(A) + sketch(B) = sketch(A ++ B);
+    """Count Sketch is linear (Sec. 1.3): sketch(A) + sketch(B) = sketch(A ++ B);
     the threaded oracle equals the single-threaded one."""
     coeffs = oracle.sketch_coeffs(61, 1, 4, 3, oracle.TWO_POLY, 21)
     keys = datagen.u64_below(8, (1 << 61) - 1, 5000)
@@ -429,7 +429,7 @@ def test_exact_f2_small():
 
 
 def test_point_query_definition():
-    """Point query (Sec. 1.4): with h(x) = x in every row (injective buckets for
+    """Point query (Sec. 1.3): with h(x) = x in every row (injective buckets for
     keys < m) each row's estimate s(x) C[i(x)] is exactly f_x, so the median is
     f_x; a key sharing its bucket with nothing else reads back its own weight."""
     n, m, t = 100, 128, 3
