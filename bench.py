@@ -618,7 +618,7 @@ def run_batched(args):
         sketches.append(sk)
         jobs.append((sk, keys[a:b], wts[a:b]))
     cands = []
-    for threads in (256, 512):
+    for threads in (256, 512, 1024):
         for chunk in (1 << 15, 1 << 17, 1 << 19):
             for ratio in (2, 8, 32):
                 cands.append({"threads": threads, "chunk_keys": chunk, "smem_min_ratio": ratio})

@@ -29,7 +29,7 @@ typedef struct {
 
 /* Launch shape of a batched plan (one point of the autotuner's search space). */
 typedef struct {
-    int threads;             /* threads per block: 128, 256 or 512 */
+    int threads;             /* threads per block: a multiple of 32, 32..1024 */
     int blocks_per_sm;       /* persistent blocks per SM (0 = as many as fit) */
     uint32_t chunk_keys;     /* keys per work item (power of two, 2^10..2^24) */
     uint32_t smem_min_ratio; /* an item uses a shared-memory counter tile when it

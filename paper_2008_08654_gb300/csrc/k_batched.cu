@@ -38,7 +38,7 @@ __device__ __forceinline__ void batched_add(int* tile, long long* counters, int 
 }
 
 template <class F, int MODE, bool PS>
-__global__ void __launch_bounds__(512) k_cs_update_batched(const BatchArgs a) {
+__global__ void __launch_bounds__(1024) k_cs_update_batched(const BatchArgs a) {
     typedef FieldOps<F> Ops;
     typedef typename Ops::val_t val_t;
     typedef typename Ops::Prep Prep;
@@ -114,25 +114,25 @@ __global__ void __launch_bounds__(512) k_cs_update_batched(const BatchArgs a) {
                 big[q] = !use_tile || aw > w_safe;
             }
             if constexpr (PS) {
-                msf::P61::Pow3 xp[4];
+                // one key at a time (its powers, then the item's rows): few live
+                // registers, so up to 1024 threads per block
 #pragma unroll
-                for (int q = 0; q < 4; ++q) msf::P61::powers3(key[q], xp[q]);
-                for (int r = r0; r < r1; ++r) {
-                    const PsCoef cb = sps[(r - r0) * NF];
-                    PsCoef cs;
-                    if (MODE == CS_TWO_POLY) cs = sps[(r - r0) * NF + 1];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < 4; ++q) {
+                    if (wt[q] == 0) continue;  // ragged end of the chunk
+                    msf::P61::Pow3 xp;
+                    msf::P61::powers3(key[q], xp);
+                    for (int r = r0; r < r1; ++r) {
+                        const PsCoef cb = sps[(r - r0) * NF];
                         u32 ylo, yhi, bucket, sb;
-                        msf::P61::row_kara(xp[q], cb.lo, cb.hi, cb.nd, cb.a0, a.c2p31, a.c4, ylo, yhi);
+                        msf::P61::row_kara(xp, cb.lo, cb.hi, cb.nd, cb.a0, a.c2p31, a.c4, ylo, yhi);
                         msf::P61::bucket_sign_hl(ylo, yhi, mask, bucket, sb);
                         if (MODE == CS_TWO_POLY) {
+                            const PsCoef cs = sps[(r - r0) * NF + 1];
                             u32 unused;
-                            msf::P61::row_kara(xp[q], cs.lo, cs.hi, cs.nd, cs.a0, a.c2p31, a.c4, ylo, yhi);
+                            msf::P61::row_kara(xp, cs.lo, cs.hi, cs.nd, cs.a0, a.c2p31, a.c4, ylo, yhi);
                             msf::P61::bucket_sign_hl(ylo, yhi, mask, unused, sb);
                         }
-                        if (wt[q] != 0)
-                            batched_add(tile, job.counters, r, r0, log2m, bucket, sb, wt[q], big[q]);
+                        batched_add(tile, job.counters, r, r0, log2m, bucket, sb, wt[q], big[q]);
                     }
                 }
             } else {

@@ -62,7 +62,7 @@ extern "C" ms_status cs_batch_create(cs_batch** out, const cs_batch_job* jobs_ho
         tu = *tuning;
     else
         cs_batch_default_tuning(&tu);
-    if (tu.threads < 32 || tu.threads > 512 || tu.threads % 32 != 0) return MS_ERR_INVALID_ARG;
+    if (tu.threads < 32 || tu.threads > 1024 || tu.threads % 32 != 0) return MS_ERR_INVALID_ARG;
     if (!is_pow2(tu.chunk_keys) || tu.chunk_keys < 1024u || tu.chunk_keys > (1u << 24))
         return MS_ERR_INVALID_ARG;
     if (tu.rows_per_item < 0 || tu.rows_per_item > msk::MAX_T || tu.blocks_per_sm < 0)

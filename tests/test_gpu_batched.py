@@ -70,7 +70,8 @@ def _check(host, b=61, c=1, k=4, mode=0, times=1, extra=None):
                                     {"threads": 128, "chunk_keys": 1 << 14, "smem_min_ratio": 1000,
                                      "rows_per_item": 1, "strategy": 0},
                                     {"threads": 512, "chunk_keys": 1 << 10, "smem_min_ratio": 0,
-                                     "rows_per_item": 2, "blocks_per_sm": 1}])
+                                     "rows_per_item": 2, "blocks_per_sm": 1},
+                                    {"threads": 1024, "chunk_keys": 1 << 16, "smem_min_ratio": 2}])
 def test_batched_matches_oracle(env, tuning):
     torch, ms = env
     jobs, host = _jobs(torch, ms, 40, 5)
