@@ -80,6 +80,8 @@ def parse_args():
     ap.add_argument("--keys", type=int, default=0,
                     help="override the workload's keys per step (small cases for profiling)")
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batched workload: use the library's default tuning instead of tuning")
     return ap.parse_args()
 
 
@@ -622,7 +624,10 @@ def run_batched(args):
         for chunk in (1 << 15, 1 << 17, 1 << 19):
             for ratio in (2, 8, 32):
                 cands.append({"threads": threads, "chunk_keys": chunk, "smem_min_ratio": ratio})
-    best, times = ms.tune_batched(jobs, cands, reps=2)
+    if args.no_tune:
+        best, times, cands = ms.default_tuning().as_dict(), [], []
+    else:
+        best, times = ms.tune_batched(jobs, cands, reps=2)
     plan = ms.Batch(jobs, best)
 
     def reset_all():

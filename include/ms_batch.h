@@ -42,13 +42,17 @@ typedef struct {
 
 typedef struct cs_batch cs_batch;
 
-/* Built-in launch shape used when `tuning` is NULL. */
+/* Built-in launch shape used when `tuning` is NULL: 1024 threads, blocks
+ * from occupancy, 2^19-key chunks, shared-memory tiles when a chunk has at
+ * least 2 m keys, all rows per item, power sum (the tuner's pick for the
+ * 4096-sketch workload on GB300). */
 ms_status cs_batch_default_tuning(cs_batch_tuning* out);
 
 /*
  * cs_batch_create -- a reusable plan that applies `count` jobs (host array) in
  * one persistent kernel launch.  All sketches must share the prime, k and mode
- * and have a power-of-two number of buckets (no CS_ANY_R; else INVALID_ARG).  The job table is copied to the device; the plan owns a
+ * and have a power-of-two number of buckets (no CS_ANY_R; else INVALID_ARG).
+ * The job table is copied to the device; the plan owns a
  * small device allocation (job table and work counter) and a CUDA graph of
  * [work-counter reset, persistent kernel].  The keys, weights and sketches must
  * stay alive while the plan is used.  Errors: INVALID_ARG, MISALIGNED, OOM, CUDA.

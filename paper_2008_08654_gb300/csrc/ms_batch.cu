@@ -43,10 +43,10 @@ void destroy_plan(cs_batch* b) {
 
 extern "C" ms_status cs_batch_default_tuning(cs_batch_tuning* out) {
     if (!out) return MS_ERR_INVALID_ARG;
-    out->threads = 512;
+    out->threads = 1024;
     out->blocks_per_sm = 0;
-    out->chunk_keys = 1u << 17;
-    out->smem_min_ratio = 8;
+    out->chunk_keys = 1u << 19;
+    out->smem_min_ratio = 2;
     out->rows_per_item = 0;
     out->strategy = msk::STRAT_POWER_SUM;
     return MS_OK;
