@@ -36,7 +36,7 @@ using msi::cuda_fail;
 // (two such blocks fit an SM).
 static const size_t kSmemTileBudget = 112 * 1024;
 static const int kMaxReplicas = 32;   // replicas a large sketch owns (<= 64 MiB)
-static const int kDefaultReplicas = 32;  // replicas a default launch uses
+static const int kDefaultReplicas = 16;  // replicas a default launch uses
 static const int kHotLog2 = 12;          // hot-key table: 4096 slots (48 KiB) per block
 
 namespace {
@@ -529,6 +529,9 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
             cfg.cluster = cl;
     }
     cfg.place = place;
+    // global placement: 512-thread blocks (measured on the 2^28-key Zipf sketch:
+    // 3% faster than 256 with 16 replicas)
+    if (ov.threads <= 0 && place == msk::PLACE_GLOBAL) cfg.threads = 512;
     cfg.replicas = 0;
     if (place == msk::PLACE_GLOBAL && !direct && sk->nrep > 0) {
         int r = ov.replicas > 0 ? ov.replicas : kDefaultReplicas;
