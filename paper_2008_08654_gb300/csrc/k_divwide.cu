@@ -131,6 +131,155 @@ __global__ void __launch_bounds__(256) k_divwide(const u64* __restrict__ v, int 
 
 constexpr int kDivWideV = 4;
 
+// ---------------------------------------------------------------------------
+// Limb-aligned b (b = 64 NB: the Table 2 sizes from 64 to 1024): one value per
+// thread, limbs in registers, so a shift by b is a renaming of limbs and the
+// carries ride the integer adds.  A block's values are contiguous in memory;
+// they are staged through shared memory with coalesced 8-byte accesses (one
+// padding limb per value keeps the per-thread reads free of bank conflicts),
+// and the quotients and remainders leave the same way.
+constexpr int kAlignedThreads = 128;
+
+template <int NB>
+__global__ void __launch_bounds__(kAlignedThreads) k_divwide_aligned(const u64* __restrict__ v,
+                                                                     u64* q, u64* r, u64 n, u64 c,
+                                                                     int steps) {
+    constexpr int L = 2 * NB;       // limbs of v
+    constexpr int LQ = NB + 1;      // limbs of the quotient (< 2^(b+1))
+    constexpr int LDS = L + 1;      // padded stride in shared memory
+    extern __shared__ u64 stage[];  // kAlignedThreads * LDS limbs
+    const u64 base = (u64)blockIdx.x * kAlignedThreads;
+    const int nv = (int)(n - base < (u64)kAlignedThreads ? n - base : (u64)kAlignedThreads);
+
+    for (int e = threadIdx.x; e < nv * L; e += kAlignedThreads)
+        stage[(e / L) * LDS + (e % L)] = __ldcs(v + base * L + e);
+    __syncthreads();
+
+    const int i = threadIdx.x;
+    u64 x[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) x[j] = i < nv ? stage[i * LDS + j] : 0ull;
+
+    // v' = v + c, with its carry out of the top limb
+    u64 vp[L];
+    u64 carry = c;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        const unsigned __int128 s = (unsigned __int128)x[j] + carry;
+        vp[j] = (u64)s;
+        carry = (u64)(s >> 64);
+    }
+    const u64 cv = carry;
+    // z = v' >> b
+    u64 z[LQ];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) z[j] = vp[NB + j];
+    z[NB] = cv;
+    // z = (z c + v') >> b, steps - 1 times
+    for (int it = 1; it < steps; ++it) {
+        u64 t[L];
+        u64 cy = 0;
+        if (c == 1) {
+#pragma unroll
+            for (int j = 0; j < L; ++j) {
+                const unsigned __int128 s = (unsigned __int128)vp[j] + (j < LQ ? z[j] : 0ull) + cy;
+                t[j] = (u64)s;
+                cy = (u64)(s >> 64);
+            }
+        } else {
+            u64 mcarry = 0;  // z c, limb by limb (c < 2^32), added into v'
+#pragma unroll
+            for (int j = 0; j < L; ++j) {
+                u64 zc = 0;
+                if (j <= LQ) {
+                    const unsigned __int128 pr =
+                        (unsigned __int128)(j < LQ ? z[j] : 0ull) * c + mcarry;
+                    zc = (u64)pr;
+                    mcarry = (u64)(pr >> 64);
+                }
+                const unsigned __int128 s = (unsigned __int128)vp[j] + zc + cy;
+                t[j] = (u64)s;
+                cy = (u64)(s >> 64);
+            }
+        }
+        cy += cv;  // the carry of v' itself (the sum stays below 2^(2b+1))
+#pragma unroll
+        for (int j = 0; j < NB; ++j) z[j] = t[NB + j];
+        z[NB] = cy;
+    }
+    // y = (v + z c) mod 2^b
+    u64 y[NB];
+    {
+        u64 cy = 0, mcarry = 0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            u64 zc;
+            if (c == 1) {
+                zc = z[j];
+            } else {
+                const unsigned __int128 pr = (unsigned __int128)z[j] * c + mcarry;
+                zc = (u64)pr;
+                mcarry = (u64)(pr >> 64);
+            }
+            const unsigned __int128 s = (unsigned __int128)x[j] + zc + cy;
+            y[j] = (u64)s;
+            cy = (u64)(s >> 64);
+        }
+    }
+
+    // quotients (LQ limbs) then remainders (NB limbs), staged and stored coalesced
+    __syncthreads();
+    if (q) {
+#pragma unroll
+        for (int j = 0; j < LQ; ++j) stage[i * LDS + j] = z[j];
+        __syncthreads();
+        for (int e = threadIdx.x; e < nv * LQ; e += kAlignedThreads)
+            q[base * LQ + e] = stage[(e / LQ) * LDS + (e % LQ)];
+        __syncthreads();
+    }
+    if (r) {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) stage[i * LDS + j] = y[j];
+        __syncthreads();
+        for (int e = threadIdx.x; e < nv * NB; e += kAlignedThreads)
+            r[base * NB + e] = stage[(e / NB) * LDS + (e % NB)];
+    }
+}
+
+template <int NB>
+cudaError_t launch_aligned(const u64* v, u64* q, u64* r, u64 n, u64 c, int steps,
+                           cudaStream_t stream) {
+    const size_t smem = (size_t)kAlignedThreads * (2 * NB + 1) * 8;
+    auto kern = k_divwide_aligned<NB>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const u64 blocks = (n + kAlignedThreads - 1) / kAlignedThreads;
+    if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    kern<<<(unsigned)blocks, kAlignedThreads, smem, stream>>>(v, q, r, n, c, steps);
+    return cudaGetLastError();
+}
+
+// 32 <= b < 64: v < 2^(2b) fits 128 bits, so one thread does the whole
+// division in unsigned __int128 (v + c cannot overflow), reading one or two
+// limbs and writing one limb of quotient (< 2^(b+1) <= 2^64) and remainder.
+__global__ void __launch_bounds__(256) k_divwide_narrow(const u64* __restrict__ v, int lv, u64* q,
+                                                        u64* r, u64 n, int b, u64 c, int steps) {
+    typedef unsigned __int128 u128;
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u128 x = (u128)__ldcs(v + i * (u64)lv);
+    if (lv == 2) x |= (u128)__ldcs(v + i * (u64)lv + 1) << 64;
+    x &= (((u128)1) << (2 * b)) - 1;  // v mod 2^(2b)
+    const u128 vp = x + c;
+    u128 z = vp >> b;
+    for (int it = 1; it < steps; ++it) z = (z * c + vp) >> b;
+    if (q) q[i] = (u64)z;
+    if (r) r[i] = (u64)((x + z * c) & ((((u128)1) << b) - 1));
+}
+
 int limbs(int bits) { return (bits + 63) / 64; }
 
 }  // namespace
@@ -158,6 +307,30 @@ extern "C" ms_status ms_div_wide(int b, uint64_t c, const uint64_t* v_dev, uint6
     if (((uintptr_t)v_dev | (uintptr_t)q_dev | (uintptr_t)r_dev) & 7u) return MS_ERR_MISALIGNED;
     const int steps = ms_div_wide_steps(b, c);
     if (steps < 1 || steps > 64) return MS_ERR_INVALID_ARG;
+    if (b < 64) {  // the whole value fits 128 bits: one value per thread
+        const u64 blocks = (n + 255) / 256;
+        if (blocks > 0x7FFFFFFFull) return MS_ERR_INVALID_ARG;
+        k_divwide_narrow<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+            (const u64*)v_dev, limbs(2 * b), (u64*)q_dev, (u64*)r_dev, (u64)n, b, (u64)c, steps);
+        const cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? MS_OK : msi::cuda_fail(e, "ms_div_wide");
+    }
+    if (b % 64 == 0) {  // limb-aligned sizes: one value per thread
+        const u64* vv = (const u64*)v_dev;
+        u64 *qq = (u64*)q_dev, *rr = (u64*)r_dev;
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e = cudaSuccess;
+        switch (b / 64) {
+            case 1: e = launch_aligned<1>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
+            case 2: e = launch_aligned<2>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
+            case 4: e = launch_aligned<4>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
+            case 8: e = launch_aligned<8>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
+            case 16: e = launch_aligned<16>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
+            default: goto general;  // other multiples of 64: the warp-segment kernel
+        }
+        return e == cudaSuccess ? MS_OK : msi::cuda_fail(e, "ms_div_wide");
+    }
+general:
     const int lv = limbs(2 * b), lq = limbs(b + 1), lr = limbs(b);
     // segment: the limbs of v, and of z*c (b + 1 + 32 bits), as a power of two
     int need = lv > limbs(b + 33) ? lv : limbs(b + 33);
