@@ -212,19 +212,15 @@ struct P61 {
     }
 
     // Bucket and sign bit of the canonical residue of a lazy y = (yhi:ylo)
-    // < 2^61 + 8.  Only y in [p, 2^61 + 8) needs the subtraction (then
-    // yhi >= 0x1FFFFFFF; the result is below 9, sign 0).  Otherwise yhi < 2^29
-    // and bit 60 is yhi >> 28.
+    // < 2^61 + 8, branch free.  y >= p exactly when y + 1 >= 2^61, i.e. when
+    // over = (y + 1) >> 61 = ((y + 1) >> 32) >> 29 is 1; then the residue is
+    // y - p = y + 1 - 2^61 < 9, whose low bits are those of ylo + 1 and whose
+    // bit 60 is 0.  Otherwise yhi < 2^29 and bit 60 is yhi >> 28.
     __device__ static __forceinline__ void bucket_sign_hl(u32 ylo, u32 yhi, u32 mask, u32& bucket,
                                                           u32& sign) {
-        if (yhi >= 0x1FFFFFFFu) {
-            u64 y = ((u64)yhi << 32) | ylo;
-            y = canon(y);
-            ylo = (u32)y;
-            yhi = (u32)(y >> 32);
-        }
-        bucket = ylo & mask;
-        sign = yhi >> 28;
+        const u32 over = ((ylo == 0xFFFFFFFFu) ? yhi + 1u : yhi) >> 29;
+        bucket = (ylo + over) & mask;
+        sign = over ? 0u : (yhi >> 28);
     }
 };
 
