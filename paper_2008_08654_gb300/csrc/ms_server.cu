@@ -384,8 +384,13 @@ extern "C" ms_status ms_server_create(ms_server** out, const ms_server_config* c
         if (e != cudaSuccess) st = msi::cuda_fail(e, "ms_server_create");
     }
     if (st == MS_OK) {
+        // Serving batches are small and latency matters: shorter chunks than the
+        // throughput default, so a batch of a few updates still spreads over
+        // every SM.
         cs_batch_tuning tu;
         cs_batch_default_tuning(&tu);
+        tu.chunk_keys = 1u << 16;
+        tu.smem_min_ratio = 8;
         const int rpi = std::min(tu.rows_per_item == 0 ? msk::MAX_T : tu.rows_per_item, max_t);
         msk::BatchArgs& a = s->args_proto;
         a.k = cfg->k;
