@@ -13,8 +13,9 @@ cs_estimate_f2 (every step of the path, in the library's kernels).
 `value` is whole-job keys/s with the keys already resident in HBM (2 GiB per
 rank, far larger than the 129 MB L2, so no flush is needed between steps).
 `e2e` is the same metric through the C ABI from pinned host buffers: each step
-copies its keys host->device, updates, estimates F2 and reads the 16-byte
-estimate back.  `roofline` is for the dominant kernel (k_cs_update), timed by
+calls cs_update_host (the library copies the keys host->device in chunks,
+overlapped with the updates), estimates F2 and reads the 16-byte estimate
+back.  `roofline` is for the dominant kernel (k_cs_update), timed by
 CUDA events on its own stream.  `cpu_baseline` (rank 0, N=1) times the CPU
 oracle on a bounded sample of the same stream on this host's cores.
 --impl reference times the CPU oracle alone (this method has no other
@@ -250,17 +251,14 @@ def run_ours(args, wl):
     # e2e through the C ABI from pinned host buffers (copies in the timed region)
     keys_h = torch.from_numpy(keys_np.view(np.int64)).pin_memory()
     w_h = None if w_np is None else torch.from_numpy(w_np).pin_memory()
-    keys_d = torch.empty_like(keys)
-    w_d = None if w is None else torch.empty_like(w)
     f2_h = torch.empty(2, dtype=torch.int64).pin_memory()
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
 
     def e2e_step():
-        keys_d.copy_(keys_h, non_blocking=True)
-        if w_d is not None:
-            w_d.copy_(w_h, non_blocking=True)
+        # cs_update_host: the library streams the host arrays in, copy and
+        # update overlapped chunk by chunk
         sk.reset()
-        sk.update(keys_d, w_d)
+        sk.update_host(keys_h, w_h)
         sk.estimate_f2(out=f2_out)
         f2_h.copy_(f2_out, non_blocking=True)
         stream.synchronize()

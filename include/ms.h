@@ -222,6 +222,26 @@ ms_status cs_update(cs_sketch* sk, const void* keys_dev, const int32_t* weights_
                     void* stream);
 
 /*
+ * cs_update_host -- cs_update for a stream held in HOST memory.  The library
+ * copies it to the GPU in chunks of 2^24 keys on a copy stream of its own,
+ * double-buffered, so the copy of one chunk overlaps the update of the one
+ * before; all chunks add into the same counters (the sketch is linear in its
+ * stream), so the result equals cs_update on the whole stream.
+ *  keys_host: n keys of the prime's key type; weights_host: n int32 weights or
+ *  NULL.  Page-locked (pinned) host memory lets the copies run asynchronously;
+ *  pageable memory works but each copy then blocks the calling thread.
+ *  The work is enqueued on `stream` (the copies wait for the work already on it,
+ *  and `stream` waits for the copies): the host buffers must stay valid until
+ *  `stream` has been synchronized.
+ *  On first use the sketch allocates two staging chunks in device memory
+ *  (2 * 2^24 * (key bytes + 4) bytes), a copy stream and four events, kept
+ *  until cs_destroy.  Calls on one sketch must not overlap.
+ *  Errors: INVALID_ARG, OOM, CUDA.
+ */
+ms_status cs_update_host(cs_sketch* sk, const void* keys_host, const int32_t* weights_host,
+                         size_t n, void* stream);
+
+/*
  * cs_estimate_f2 -- Output of Algorithm count-sketch per row, X_r = sum_i
  * C[r][i]^2 (computed modulo 2^128), and the F2 estimate = the median of the t
  * row values (t odd, so the middle one).  Writes one ms_u128 to out_dev

@@ -13,6 +13,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -81,6 +83,7 @@ def _load():
         "cs_row_stride": (i, [vp, ctypes.POINTER(u32)]),
         "cs_coeffs": (i, [vp, vp]),
         "cs_update": (i, [vp, vp, vp, sz, vp]),
+        "cs_update_host": (i, [vp, vp, vp, sz, vp]),
         "cs_estimate_f2": (i, [vp, vp, vp, vp]),
         "cs_point_query": (i, [vp, vp, vp, sz, vp]),
         "cs_counters": (i, [vp, pp]),
@@ -151,6 +154,21 @@ def _nkeys(keys: torch.Tensor, b: int, c: int) -> int:
     if total % kb:
         raise ValueError("key tensor size is not a multiple of the %d-byte key type" % kb)
     return total // kb
+
+
+def _host_buffer(a, kb: int):
+    """(pointer, element count of kb bytes) of a contiguous host numpy array or
+    CPU tensor."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("expected a contiguous host tensor")
+        total, ptr = a.numel() * a.element_size(), a.data_ptr()
+    else:
+        a = np.ascontiguousarray(a)
+        total, ptr = a.nbytes, a.ctypes.data
+    if total % kb:
+        raise ValueError("host buffer size is not a multiple of %d bytes" % kb)
+    return ptr, total // kb
 
 
 def _u128_array(values):
@@ -320,6 +338,21 @@ class Sketch:
             raise TypeError("weights must be int32")
         _check(_load().cs_update(self._h, _ptr(keys), _ptr(weights), n, _stream(stream)),
                "cs_update")
+
+    def update_host(self, keys, weights=None, stream=None):
+        """cs_update_host: keys (and int32 weights) in host memory -- numpy arrays
+        or CPU tensors, pinned for asynchronous copies.  Keep them alive until
+        `stream` is synchronized."""
+        kp, n = _host_buffer(keys, key_dtype_bytes(self.b, self.c))
+        wp = None
+        if weights is not None:
+            wp, nw = _host_buffer(weights, 4)
+            if nw != n:
+                raise ValueError("weights must have one entry per key")
+            if (weights.dtype != torch.int32) if isinstance(weights, torch.Tensor) else \
+                    (np.asarray(weights).dtype != np.int32):
+                raise TypeError("weights must be int32")
+        _check(_load().cs_update_host(self._h, kp, wp, n, _stream(stream)), "cs_update_host")
 
     def estimate_f2(self, out: torch.Tensor | None = None, rows: torch.Tensor | None = None,
                     stream=None) -> torch.Tensor:

@@ -330,6 +330,16 @@ static int ilog2_exact(uint32_t m) {
 static void sketch_free_device(cs_sketch* sk) {
     if (sk->block) cudaFree(sk->block);
     sk->block = nullptr;
+    if (sk->hcopy) cudaStreamSynchronize(sk->hcopy);
+    for (int i = 0; i < 2; ++i) {
+        if (sk->hcopied[i]) cudaEventDestroy(sk->hcopied[i]);
+        if (sk->hfree[i]) cudaEventDestroy(sk->hfree[i]);
+        sk->hcopied[i] = sk->hfree[i] = nullptr;
+    }
+    if (sk->hcopy) cudaStreamDestroy(sk->hcopy);
+    sk->hcopy = nullptr;
+    if (sk->hstage) cudaFree(sk->hstage);
+    sk->hstage = nullptr;
 }
 
 static uint32_t next_pow2(uint32_t m) {
@@ -654,6 +664,74 @@ extern "C" ms_status cs_update(cs_sketch* sk, const void* keys_dev, const int32_
         MS_CUDA(msk::launch_reduce_replicas(sk->counters, sk->replicas, cfg.replicas,
                                             (u64)sk->t * sk->m, (cudaStream_t)stream),
                 "cs_update replicas");
+    sk->last_cfg = cfg;
+    sk->last_specialized = spec;
+    return MS_OK;
+}
+
+static const uint64_t kHostChunk = 1ull << 24;  // keys per staging chunk of cs_update_host
+
+extern "C" ms_status cs_update_host(cs_sketch* sk, const void* keys_host, const int32_t* weights_host,
+                                    size_t n, void* stream) {
+    if (!sk) return MS_ERR_INVALID_ARG;
+    if (n == 0) return MS_OK;
+    if (!keys_host) return MS_ERR_INVALID_ARG;
+    const size_t kb = key_bytes(sk->prime);
+    const size_t chunk_bytes = (size_t)kHostChunk * (kb + 4);  // keys, then weights
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!sk->hstage) {
+        ms_status a = dev_alloc(&sk->hstage, 2 * chunk_bytes);
+        if (a != MS_OK) return a;
+        cudaError_t e = cudaStreamCreateWithFlags(&sk->hcopy, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaEventCreateWithFlags(&sk->hcopied[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sk->hfree[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            cudaFree(sk->hstage);
+            sk->hstage = nullptr;
+            return cuda_fail(e, "cs_update_host setup");
+        }
+    }
+    // one configuration for the whole stream: replica counters are sized for
+    // all n keys and reduced once at the end
+    msk::UpdateArgs a;
+    memset(&a, 0, sizeof(a));
+    msk::LaunchCfg cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    ms_status stt = choose_update_config(sk, n, weights_host == nullptr, a, cfg);
+    if (stt != MS_OK) return stt;
+    // the copies start after the work already on `stream` (which may still read
+    // the staging chunks of an earlier call)
+    MS_CUDA(cudaEventRecord(sk->hfree[0], st), "cs_update_host");
+    MS_CUDA(cudaEventRecord(sk->hfree[1], st), "cs_update_host");
+    const char* kh = (const char*)keys_host;
+    int spec = 0;
+    for (uint64_t off = 0, c = 0; off < n; off += kHostChunk, ++c) {
+        const int buf = (int)(c & 1);
+        const uint64_t len = (n - off) < kHostChunk ? (n - off) : kHostChunk;
+        char* kd = (char*)sk->hstage + (size_t)buf * chunk_bytes;
+        int32_t* wd = (int32_t*)(kd + (size_t)kHostChunk * kb);
+        MS_CUDA(cudaStreamWaitEvent(sk->hcopy, sk->hfree[buf], 0), "cs_update_host");
+        MS_CUDA(cudaMemcpyAsync(kd, kh + off * kb, len * kb, cudaMemcpyHostToDevice, sk->hcopy),
+                "cs_update_host copy");
+        if (weights_host)
+            MS_CUDA(cudaMemcpyAsync(wd, weights_host + off, len * 4, cudaMemcpyHostToDevice,
+                                    sk->hcopy),
+                    "cs_update_host copy");
+        MS_CUDA(cudaEventRecord(sk->hcopied[buf], sk->hcopy), "cs_update_host");
+        MS_CUDA(cudaStreamWaitEvent(st, sk->hcopied[buf], 0), "cs_update_host");
+        a.keys = kd;
+        a.weights = weights_host ? wd : nullptr;
+        a.n = len;
+        a.vec_ok = 1;  // staging chunks are 256-byte aligned
+        MS_CUDA(msk::launch_cs_update(sk->prime, a, sk->words.data(), cfg, st, &spec), "cs_update_host");
+        MS_CUDA(cudaEventRecord(sk->hfree[buf], st), "cs_update_host");
+    }
+    if (a.replicas)
+        MS_CUDA(msk::launch_reduce_replicas(sk->counters, sk->replicas, cfg.replicas,
+                                            (u64)sk->t * sk->m, st),
+                "cs_update_host replicas");
     sk->last_cfg = cfg;
     sk->last_specialized = spec;
     return MS_OK;

@@ -1,6 +1,7 @@
 // Internal host-side state of the library's handles.  Not installed.
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <vector>
@@ -34,6 +35,11 @@ struct cs_sketch {
     int f2_splits = 1;
     int* replicas = nullptr;          // update scratch: nrep int32 copies of the counters
     int nrep = 0;                     // (large sketches only; zero between calls)
+    // cs_update_host: two staging chunks, a copy stream and its events (lazy)
+    void* hstage = nullptr;
+    cudaStream_t hcopy = nullptr;
+    cudaEvent_t hcopied[2] = {nullptr, nullptr};
+    cudaEvent_t hfree[2] = {nullptr, nullptr};
     LaunchOverride launch;
     msk::LaunchCfg last_cfg = {};
     int last_specialized = 0;
