@@ -380,9 +380,9 @@ __device__ __forceinline__ void apply_fast(int* tile, u32 tile_saddr, long long*
 // Bucket and sign bit of row r for p = 2^61-1, k = 4 (Karatsuba power sum):
 // two-for-one (both from one polynomial) or two polynomials (the sign from the
 // second one's bit 60).
-template <int NF, class PC>
+template <int NF, bool ANY = false, class PC>
 __device__ __forceinline__ void p61_row_bs(const msf::P61::Pow3& xp, const PC& pc, int r, u32 mask,
-                                           u32& bucket, u32& sign) {
+                                           u32 arb_r, u32& bucket, u32& sign) {
     typedef msf::P61 F;
     const int fb = r * NF;
     u32 ylo, yhi;
@@ -392,7 +392,13 @@ __device__ __forceinline__ void p61_row_bs(const msf::P61::Pow3& xp, const PC& p
         const int nd[3] = {pc.nd[fb * 4 + 1], pc.nd[fb * 4 + 2], pc.nd[fb * 4 + 3]};
         F::row_kara(xp, al, ah, nd, pc.w[fb * 4], pc.c2p31, pc.c4, ylo, yhi);
     }
-    F::bucket_sign_hl(ylo, yhi, mask, bucket, sign);
+    if (ANY) {  // Algorithm Mersenne-arb-r on the canonical value
+        u32 a;
+        F::arb_split(F::canon_hl(ylo, yhi), arb_r, bucket, a);
+        sign = a ^ 1u;  // s = 2a - 1: subtract when a = 0
+    } else {
+        F::bucket_sign_hl(ylo, yhi, mask, bucket, sign);
+    }
     if (NF == 2) {
         const int fs = fb + 1;
         const u32 sl[3] = {pc.lo[fs * 4 + 1], pc.lo[fs * 4 + 2], pc.lo[fs * 4 + 3]};
@@ -534,7 +540,7 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
             big[q] = !unit_safe && aw > w_safe;
         }
 
-        if constexpr (!GENERIC && STRAT == STRAT_POWER_SUM && std::is_same<F, msf::P61>::value &&
+        if constexpr (!GENERIC && STRAT >= STRAT_POWER_SUM && std::is_same<F, msf::P61>::value &&
                       K == 4) {
             // Keys whose weight could overflow an int32 tile counter (rare)
             // go straight to the int64 counters; the hot loops below see
@@ -557,7 +563,8 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         u32 bucket, sb;
-                        p61_row_bs<NF>(xp[q], pc, r, mask, bucket, sb);
+                        p61_row_bs<NF, STRAT == STRAT_POWER_SUM_ANY_R>(xp[q], pc, r, mask, a.arb_r,
+                                                                       bucket, sb);
                         apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket,
                                           sb ? -wt[q] : wt[q], log2m, lcs);
                     }
@@ -573,7 +580,8 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
 #pragma unroll
                     for (int r = 0; r < T; ++r) {
                         u32 bucket, sb;
-                        p61_row_bs<NF>(xp, pc, r, mask, bucket, sb);
+                        p61_row_bs<NF, STRAT == STRAT_POWER_SUM_ANY_R>(xp, pc, r, mask, a.arb_r,
+                                                                       bucket, sb);
                         const int d = (int)sb * w2 + w;
                         if (PLACE == PLACE_SMEM) {
                             asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(rbase + (bucket << 2)), "r"(d)

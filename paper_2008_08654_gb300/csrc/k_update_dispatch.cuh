@@ -77,27 +77,30 @@ static cudaError_t launch_exact(const UpdateArgs& a, const u64* coef_host, const
     return cudaLaunchKernelEx(&lc, kern, a, pc);
 }
 
+template <class F, int T, int K, int MODE, int PLACE>
+static cudaError_t launch_strat(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
+                                cudaStream_t stream, int* occupancy) {
+    constexpr bool PS_OK = std::is_same<F, msf::P61>::value && K == 4;
+    if (PS_OK && cfg.strategy == STRAT_POWER_SUM) {
+        if (a.arb_r)
+            return launch_exact<F, T, K, MODE, PLACE, PS_OK ? STRAT_POWER_SUM_ANY_R : STRAT_HORNER>(
+                a, coef_host, cfg, stream, occupancy);
+        return launch_exact<F, T, K, MODE, PLACE, PS_OK ? STRAT_POWER_SUM : STRAT_HORNER>(
+            a, coef_host, cfg, stream, occupancy);
+    }
+    return launch_exact<F, T, K, MODE, PLACE, STRAT_HORNER>(a, coef_host, cfg, stream, occupancy);
+}
+
 template <class F, int T, int K, int MODE>
 static cudaError_t launch_place(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
                                 cudaStream_t stream, int* occupancy) {
-    constexpr bool PS_OK = std::is_same<F, msf::P61>::value && K == 4;
-    const bool ps = PS_OK && cfg.strategy == STRAT_POWER_SUM;
     switch (cfg.place) {
         case PLACE_SMEM:
-            return ps ? launch_exact<F, T, K, MODE, PLACE_SMEM, PS_OK ? STRAT_POWER_SUM : STRAT_HORNER>(
-                            a, coef_host, cfg, stream, occupancy)
-                      : launch_exact<F, T, K, MODE, PLACE_SMEM, STRAT_HORNER>(a, coef_host, cfg,
-                                                                              stream, occupancy);
+            return launch_strat<F, T, K, MODE, PLACE_SMEM>(a, coef_host, cfg, stream, occupancy);
         case PLACE_DSMEM:
-            return ps ? launch_exact<F, T, K, MODE, PLACE_DSMEM, PS_OK ? STRAT_POWER_SUM : STRAT_HORNER>(
-                            a, coef_host, cfg, stream, occupancy)
-                      : launch_exact<F, T, K, MODE, PLACE_DSMEM, STRAT_HORNER>(a, coef_host, cfg,
-                                                                               stream, occupancy);
+            return launch_strat<F, T, K, MODE, PLACE_DSMEM>(a, coef_host, cfg, stream, occupancy);
         default:
-            return ps ? launch_exact<F, T, K, MODE, PLACE_GLOBAL, PS_OK ? STRAT_POWER_SUM : STRAT_HORNER>(
-                            a, coef_host, cfg, stream, occupancy)
-                      : launch_exact<F, T, K, MODE, PLACE_GLOBAL, STRAT_HORNER>(a, coef_host, cfg,
-                                                                                stream, occupancy);
+            return launch_strat<F, T, K, MODE, PLACE_GLOBAL>(a, coef_host, cfg, stream, occupancy);
     }
 }
 
@@ -114,7 +117,11 @@ static cudaError_t launch_mode(const UpdateArgs& a, const u64* coef_host, const 
 template <class F>
 cudaError_t launch_update_for(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
                               cudaStream_t stream, int* specialized, int* occupancy) {
-    if (update_is_specialized(a.t, a.k, a.arb_r)) {
+    constexpr int PRIME = std::is_same<F, msf::P31>::value   ? PRIME_31
+                          : std::is_same<F, msf::P61>::value ? PRIME_61
+                          : std::is_same<F, msf::P89>::value ? PRIME_89
+                                                             : PRIME_64_59;
+    if (update_is_specialized(PRIME, a.t, a.k, a.arb_r)) {
         if (specialized) *specialized = 1;
         return a.t == 5 ? launch_mode<F, 5, 4>(a, coef_host, cfg, stream, occupancy)
                         : launch_mode<F, 7, 4>(a, coef_host, cfg, stream, occupancy);

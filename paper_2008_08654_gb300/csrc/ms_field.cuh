@@ -216,6 +216,12 @@ struct P61 {
     // over = (y + 1) >> 61 = ((y + 1) >> 32) >> 29 is 1; then the residue is
     // y - p = y + 1 - 2^61 < 9, whose low bits are those of ylo + 1 and whose
     // bit 60 is 0.  Otherwise yhi < 2^29 and bit 60 is yhi >> 28.
+    // The canonical residue of a lazy y = (yhi:ylo) < 2^61 + 8 (same test as below).
+    __device__ static __forceinline__ u64 canon_hl(u32 ylo, u32 yhi) {
+        const u32 over = ((ylo == 0xFFFFFFFFu) ? yhi + 1u : yhi) >> 29;
+        return over ? (u64)(ylo + 1u) : (((u64)yhi << 32) | ylo);
+    }
+
     __device__ static __forceinline__ void bucket_sign_hl(u32 ylo, u32 yhi, u32 mask, u32& bucket,
                                                           u32& sign) {
         const u32 over = ((ylo == 0xFFFFFFFFu) ? yhi + 1u : yhi) >> 29;

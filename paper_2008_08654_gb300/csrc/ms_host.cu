@@ -508,7 +508,7 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
     const LaunchOverride& ov = sk->launch;
     const int nf = (sk->mode & CS_TWO_POLY) ? 2 : 1;
     const size_t coef_bytes = (size_t)sk->t * nf * sk->k * words_per_value(sk->prime) * 8;
-    const bool generic = !msk::update_is_specialized(sk->t, sk->k, sk->r);
+    const bool generic = !msk::update_is_specialized(sk->prime, sk->t, sk->k, sk->r);
     const size_t extra = generic ? (coef_bytes + 15) / 16 * 16 : 0;
     const size_t tile_bytes = (size_t)sk->t * sk->m * 4;
     const size_t optin = (size_t)d.smem_optin;

@@ -25,7 +25,8 @@ enum Place {
 // Row-hash evaluation strategy (both give the same canonical value).
 enum Strategy {
     STRAT_HORNER = 0,    // Algorithm Mersenne, k-1 lazy multiply-add steps per row
-    STRAT_POWER_SUM = 1  // x^2..x^(k-1) once per key, then sum a_i x^i per row
+    STRAT_POWER_SUM = 1, // x^2..x^(k-1) once per key, then sum a_i x^i per row
+    STRAT_POWER_SUM_ANY_R = 2  // internal: the power sum with the any-m bucket map
 };
 
 constexpr int MAX_T = 15;
@@ -56,8 +57,8 @@ struct UpdateArgs {
 // parameter space) or the generic one (coefficients staged in shared memory
 // after the counter tile, which the launch's shared memory must cover).  The
 // host's launch choice and the dispatcher both ask this one function.
-inline bool update_is_specialized(int t, int k, u32 arb_r) {
-    return arb_r == 0 && k == 4 && (t == 5 || t == 7);
+inline bool update_is_specialized(int prime, int t, int k, u32 arb_r) {
+    return k == 4 && (t == 5 || t == 7) && (arb_r == 0 || prime == PRIME_61);
 }
 
 // Launch configuration chosen on the host.
