@@ -60,6 +60,15 @@ WORKLOADS = {
                             "(any-m map of Algorithm Mersenne-arb-r)"),
 }
 
+# DRAM bytes per key of k_cs_update (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture of the workload's first 2^25 keys in the bench's launch
+# configuration; the stream's traffic grows in proportion, so a launch's traffic
+# is this times its keys.  Only workloads whose current kernel was captured.
+MEASURED_TRAFFIC_PER_KEY = {
+    "large": (297.896704e6 + 6.552832e6) / 2 ** 25,
+    "plain-2^28": (402.737920e6 + 2.999296e6) / 2 ** 25,
+}
+
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -325,7 +334,10 @@ def run_ours(args, wl):
             "peak": peak_mul / 1e9,
             "unit": "Gmul128/s",
             "frac": achieved_mul / peak_mul,
-            "traffic": None,
+            "traffic": (MEASURED_TRAFFIC_PER_KEY[args.workload] * n
+                        if args.workload in MEASURED_TRAFFIC_PER_KEY else None),
+            "traffic_unit": "bytes per launch (ncu DRAM bytes of a 2^25-key capture, scaled)",
+            "algorithmic_bytes": n * bytes_per_key,
             "kernel": "k_cs_update",
             "kernel_ms": statistics.mean(kern_ms),
             "mul128_per_key": mul128_per_key,
@@ -338,7 +350,8 @@ def run_ours(args, wl):
         },
         "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": "keys/s",
                 "h2d_bytes_per_step": n * bytes_per_key, "d2h_bytes_per_step": 16},
-        "gpu_launches": 3 * args.steps,
+        # zero, update, (replica reduce,) F2 per timed step
+        "gpu_launches": (4 if launch.get("replicas") else 3) * args.steps,
         "f2_estimate": str(f2_est),
     }
     if clk:
