@@ -315,22 +315,22 @@ extern "C" ms_status ms_div_wide(int b, uint64_t c, const uint64_t* v_dev, uint6
         const cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? MS_OK : msi::cuda_fail(e, "ms_div_wide");
     }
-    if (b % 64 == 0) {  // limb-aligned sizes: one value per thread
+    const int nb = b / 64;
+    if (b % 64 == 0 && (nb & (nb - 1)) == 0) {  // 64..1024, a power of two limbs: one value per thread
         const u64* vv = (const u64*)v_dev;
         u64 *qq = (u64*)q_dev, *rr = (u64*)r_dev;
         cudaStream_t st = (cudaStream_t)stream;
         cudaError_t e = cudaSuccess;
-        switch (b / 64) {
+        switch (nb) {
             case 1: e = launch_aligned<1>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
             case 2: e = launch_aligned<2>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
             case 4: e = launch_aligned<4>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
             case 8: e = launch_aligned<8>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
-            case 16: e = launch_aligned<16>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
-            default: goto general;  // other multiples of 64: the warp-segment kernel
+            default: e = launch_aligned<16>(vv, qq, rr, (u64)n, (u64)c, steps, st); break;
         }
         return e == cudaSuccess ? MS_OK : msi::cuda_fail(e, "ms_div_wide");
     }
-general:
+    // any other b: the warp-segment kernel
     const int lv = limbs(2 * b), lq = limbs(b + 1), lr = limbs(b);
     // segment: the limbs of v, and of z*c (b + 1 + 32 bits), as a power of two
     int need = lv > limbs(b + 33) ? lv : limbs(b + 33);
