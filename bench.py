@@ -65,7 +65,6 @@ WORKLOADS = {
 # configuration; the stream's traffic grows in proportion, so a launch's traffic
 # is this times its keys.  Only workloads whose current kernel was captured.
 MEASURED_TRAFFIC_PER_KEY = {
-    "large": (297.896704e6 + 6.552832e6) / 2 ** 25,
     "plain-2^28": (402.737920e6 + 2.999296e6) / 2 ** 25,
 }
 

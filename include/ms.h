@@ -313,21 +313,24 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  *            over a thread-block cluster's distributed shared memory,
  *            2 = global memory: int32 replicas of the counters (block b adds
  *            into replica b mod R, then one kernel adds the replicas into the
- *            int64 counters; sketches whose tile exceeds 112 KiB own R <= 8
- *            replicas, others fall back to 3), 3 = int64 atomics straight
+ *            int64 counters; a sketch whose tile exceeds 112 KiB owns up to
+ *            32 replicas, at most 64 MiB of them), 3 = int64 atomics straight
  *            into the counters.
  *  Default: 0 when the t*m int32 tile fits 112 KiB, else 2.
  *  strategy: 0 = Horner per row (Algorithm Mersenne), 1 = powers of x once per
  *            key, then sum a_i x^i per row (only for p = 2^61-1 with k = 4;
  *            other sketches use Horner).  Both give identical hash values.
- *  threads (multiple of 32, <= 512), blocks (total), blocks_per_sm (cap),
- *  cluster (power of two <= 16, place 1 only), replicas (power of two <= 32,
- *  place 2 only; capped at the replicas the sketch owns; default 32),
- *  aggregate (0, 1 or 2, default 1; unit weights and place 2 or 3 only):
- *  1 = lanes of a warp holding the same key send one atomic carrying their
+ *  threads (multiple of 32, <= 512; default 512 for place 2 and 3), blocks
+ *  (total), blocks_per_sm (cap), cluster (power of two <= 16, place 1 only),
+ *  replicas (power of two <= 32, place 2 only; capped at the replicas the
+ *  sketch owns; default 16),
+ *  aggregate (0, 1 or 2, default 2; unit weights and place 2 or 3 only):
+ *  1 = lanes of a warp holding the same key send one update carrying their
  *  count; 2 = also a per-block table of 4096 keys in shared memory (one-word
- *  keys: every prime but 2^89-1) whose counts the block adds once per row at
- *  its end.  Every key is still hashed; the counters are identical.
+ *  keys: every prime but 2^89-1): a key the table holds is only counted and is
+ *  hashed once, with its count, when the block ends; the other keys are hashed
+ *  128 at a time from a per-warp queue.  The counters are identical for every
+ *  setting (a sketch is linear in the stream).
  * Errors: INVALID_ARG.
  */
 ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int threads, int blocks,

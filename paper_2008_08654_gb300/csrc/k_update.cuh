@@ -264,40 +264,44 @@ __device__ __forceinline__ u32 match_key(const u128x& k) {
     return __match_any_sync(0xffffffffu, k.lo) & __match_any_sync(0xffffffffu, k.hi);
 }
 
-// ------------------------------------------------------------ hot-key table
+// ------------------------------------------------------------ de-duplication
 //
-// A direct-mapped table in shared memory for one-word keys: slot i holds a key
-// (or EMPTY) and how many times this block saw it.  Used only for unit weights
-// with the global placement: a key that owns its slot (or claims an empty one)
-// adds 1 to the slot's count instead of t atomics to global memory; at the end
-// the block adds each slot's count once per row.  Every key is still hashed.
-constexpr u64 HOT_EMPTY = ~0ull;
+// Unit weights, global placement, one-word keys.  A Count Sketch is linear in
+// the stream (Sec. 1.3), so c occurrences of key x add exactly what one update
+// of x with weight c adds.  Each block keeps a direct-mapped table in shared
+// memory, slot i holding a key (or DEDUP_EMPTY) and how often the block has
+// seen it: a key that owns its slot, or claims an empty one, is only counted,
+// and is hashed once, with its count, when the block has finished its share of
+// the stream.  The other keys go to their warp's queue in shared memory and
+// are hashed 128 at a time (four per lane), so the lanes of a warp hash only
+// keys the table did not absorb.
+constexpr u64 DEDUP_EMPTY = ~0ull;
 
 template <class K>
-struct HotKey {
+struct DedupKey {
     static constexpr bool OK = false;
 };
 template <>
-struct HotKey<u64> {
+struct DedupKey<u64> {
     static constexpr bool OK = true;
 };
 template <>
-struct HotKey<u32> {
+struct DedupKey<u32> {
     static constexpr bool OK = true;
 };
 
-// Returns true when the group of w occurrences was counted in the table.
-// Keys equal to EMPTY never use it.
-__device__ __forceinline__ bool hot_add(u64* hkey, int* hcnt, int log2slots, u64 key, int w) {
-    if (key == HOT_EMPTY) return false;
+// Counts c occurrences of `key` in the table; false when the key's slot holds
+// another key (or the key is DEDUP_EMPTY itself, which never enters the table).
+__device__ __forceinline__ bool dedup_count(u64* tk, int* tc, int log2slots, u64 key, int c) {
+    if (key == DEDUP_EMPTY) return false;
     const u32 slot = (u32)((key * 0x9E3779B97F4A7C15ull) >> (64 - log2slots));
-    u64 cur = hkey[slot];
-    if (cur == HOT_EMPTY) {
-        cur = atomicCAS((unsigned long long*)&hkey[slot], HOT_EMPTY, key);
-        if (cur == HOT_EMPTY) cur = key;  // claimed by this thread
+    u64 cur = tk[slot];
+    if (cur == DEDUP_EMPTY) {
+        cur = atomicCAS((unsigned long long*)&tk[slot], DEDUP_EMPTY, key);
+        if (cur == DEDUP_EMPTY) cur = key;  // claimed by this thread
     }
     if (cur != key) return false;
-    atomicAdd(&hcnt[slot], w);
+    atomicAdd(&tc[slot], c);
     return true;
 }
 
@@ -472,16 +476,21 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                     : reinterpret_cast<int*>(smem);
     const u32 tile_cells = (PLACE == PLACE_GLOBAL) ? 0u : (u32)t * mloc;
     u64* scoef = reinterpret_cast<u64*>(smem + (size_t)tile_cells * 4u);
-    // PLACE_GLOBAL: hot-key table after the coefficients
-    const int hot_log2 = (PLACE == PLACE_GLOBAL && HotKey<typename Ops::key_t>::OK &&
-                          a.weights == nullptr) ? a.hot_log2 : 0;
-    const u32 hot_slots = hot_log2 ? (1u << hot_log2) : 0u;
-    u64* hkey = reinterpret_cast<u64*>(
+    // PLACE_GLOBAL with unit weights: the de-duplication table (12 bytes a slot)
+    // and the warps' queues (12 bytes an entry) after the coefficients
+    constexpr bool DEDUP_OK = PLACE == PLACE_GLOBAL && DedupKey<typename Ops::key_t>::OK;
+    const int dd_log2 = (DEDUP_OK && a.weights == nullptr) ? a.dedup_log2 : 0;
+    const u32 dd_slots = dd_log2 ? (1u << dd_log2) : 0u;
+    u64* tk = reinterpret_cast<u64*>(
         smem + (((size_t)tile_cells * 4u + (GENERIC ? (size_t)t * NF * k * W * 8 : 0) + 15) & ~(size_t)15));
-    int* hcnt = reinterpret_cast<int*>(hkey + hot_slots);
-    for (u32 i = threadIdx.x; i < hot_slots; i += blockDim.x) {
-        hkey[i] = HOT_EMPTY;
-        hcnt[i] = 0;
+    int* tc = reinterpret_cast<int*>(tk + dd_slots);
+    u64* qk = reinterpret_cast<u64*>(tc + dd_slots) + (size_t)(threadIdx.x >> 5) * DEDUP_QCAP;
+    int* qc = reinterpret_cast<int*>(reinterpret_cast<u64*>(tc + dd_slots) +
+                                     (size_t)(blockDim.x >> 5) * DEDUP_QCAP) +
+              (threadIdx.x >> 5) * DEDUP_QCAP;
+    for (u32 i = threadIdx.x; i < dd_slots; i += blockDim.x) {
+        tk[i] = DEDUP_EMPTY;
+        tc[i] = 0;
     }
     const u32 tile_saddr = (PLACE == PLACE_GLOBAL) ? 0u : (u32)__cvta_generic_to_shared(tile);
 
@@ -503,35 +512,89 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
     const bool unit_safe = a.weights == nullptr && w_safe >= 1u;  // every weight is 0 or 1
     const u32 row_bytes = m << 2;  // PLACE_SMEM: one row of the int32 tile
     const u64 stride = (u64)gridDim.x * blockDim.x * 4ull;
-    // The loop runs on the warp's first key index, so every lane of a warp takes
-    // the same number of iterations (lanes past the end load weight-0 keys);
-    // warp-wide matching below relies on it.
-    const u64 lane4 = (u64)(threadIdx.x & 31u) * 4ull;
-    for (u64 jw = ((u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)) * 4ull; jw < n;
-         jw += stride) {
-        const u64 j = jw + lane4;
+    const u32 lane = threadIdx.x & 31u;
+    const u32 lanes_below = (1u << lane) - 1u;
+    u32 qn = 0;      // de-duplication: this warp's queue length (warp-uniform)
+    int drain = -1;  // de-duplication: -1 while streaming, then the batch being drained
+    // The loop runs on the block's first key index, so every warp of a block
+    // takes the same number of iterations (warps and lanes past the end load
+    // weight-0 keys): warp-wide matching relies on it, and so does the drain of
+    // the de-duplication table, which starts with a block barrier.
+    for (u64 jb = (u64)blockIdx.x * blockDim.x * 4ull;;) {
         typename Ops::key_t key[4];
         int wt[4];
-        KeyIO<F>::load(a.keys, j, n, vec, key);
-        load_weights4(a.weights, j, n, vec, wt);
-        if (PLACE == PLACE_GLOBAL && a.aggregate && a.weights == nullptr) {
-            // Unit weights: lanes of this warp holding the same key would add
-            // to the same t counters.  The lowest such lane adds the group's
-            // count; the others still hash their key but add nothing.
-            const u32 lane = threadIdx.x & 31u;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const u32 valid = __ballot_sync(0xffffffffu, wt[q] != 0);
-                u32 grp = match_key(key[q]) & valid;
-                if (wt[q] != 0) wt[q] = ((grp & ((1u << lane) - 1u)) == 0u) ? __popc(grp) : 0;
+        if (drain < 0) {
+            if (jb >= n) {
+                if (!DEDUP_OK || dd_log2 == 0) break;
+                drain = 0;
+                __syncthreads();  // every warp is done with the table
+                continue;
             }
-        }
-        if constexpr (HotKey<typename Ops::key_t>::OK) {
-            if (hot_log2) {
+            const u64 j = jb + (u64)threadIdx.x * 4ull;
+            jb += stride;
+            KeyIO<F>::load(a.keys, j, n, vec, key);
+            load_weights4(a.weights, j, n, vec, wt);
+            if (PLACE == PLACE_GLOBAL && a.aggregate && a.weights == nullptr) {
+                // Unit weights: lanes of this warp holding the same key would add
+                // to the same t counters.  The lowest such lane takes the group's
+                // count; the others keep weight 0.
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (wt[q] != 0 && hot_add(hkey, hcnt, hot_log2, (u64)key[q], wt[q])) wt[q] = 0;
+                for (int q = 0; q < 4; ++q) {
+                    const u32 valid = __ballot_sync(0xffffffffu, wt[q] != 0);
+                    u32 grp = match_key(key[q]) & valid;
+                    if (wt[q] != 0) wt[q] = ((grp & lanes_below) == 0u) ? __popc(grp) : 0;
+                }
             }
+            if constexpr (DEDUP_OK) {
+                if (dd_log2) {
+                    // the table counts what it can; the rest waits in the queue until
+                    // 128 keys (four a lane) are there to hash
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const bool miss = wt[q] != 0 && !dedup_count(tk, tc, dd_log2, (u64)key[q], wt[q]);
+                        const u32 mb = __ballot_sync(0xffffffffu, miss);
+                        if (miss) {
+                            const u32 pos = qn + __popc(mb & lanes_below);
+                            qk[pos] = (u64)key[q];
+                            qc[pos] = wt[q];
+                        }
+                        qn += __popc(mb);
+                    }
+                    if (qn < 128u) continue;
+                    __syncwarp();
+                    qn -= 128u;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        key[q] = (typename Ops::key_t)qk[qn + lane + 32u * q];
+                        wt[q] = qc[qn + lane + 32u * q];
+                    }
+                    __syncwarp();
+                }
+            }
+        } else if constexpr (DEDUP_OK) {
+            // batch 0: what is left in this warp's queue; then the table, four
+            // slots a thread per batch
+            if (drain == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const u32 e = lane + 32u * q;
+                    key[q] = (typename Ops::key_t)(e < qn ? qk[e] : 0ull);
+                    wt[q] = e < qn ? qc[e] : 0;
+                }
+            } else {
+                const u32 base = (u32)(drain - 1) * blockDim.x * 4u;
+                if (base >= dd_slots) break;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const u32 sl = base + threadIdx.x + blockDim.x * (u32)q;
+                    const u64 kw = sl < dd_slots ? tk[sl] : DEDUP_EMPTY;
+                    key[q] = (typename Ops::key_t)(kw == DEDUP_EMPTY ? 0ull : kw);
+                    wt[q] = kw == DEDUP_EMPTY ? 0 : tc[sl];
+                }
+            }
+            ++drain;
+        } else {
+            break;
         }
         bool big[4];
 #pragma unroll
@@ -629,37 +692,7 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
         }
     }
 
-    if (PLACE == PLACE_GLOBAL) {
-        if constexpr (HotKey<typename Ops::key_t>::OK) {
-            if (hot_log2) {
-                __syncthreads();
-                for (u32 i = threadIdx.x; i < hot_slots; i += blockDim.x) {
-                    const u64 kw = hkey[i];
-                    const int cnt = hcnt[i];
-                    if (kw == HOT_EMPTY || cnt == 0) continue;
-                    const Prep xq = Ops::prep((typename Ops::key_t)kw);
-                    for (int r = 0; r < t; ++r) {
-                        const int fb = r * NF;
-                        val_t y = MSK_COEF(fb, k - 1);
-                        for (int i2 = k - 2; i2 >= 0; --i2) y = Ops::mul_add(y, xq, MSK_COEF(fb, i2));
-                        const val_t h = Ops::canon(y);
-                        val_t g = h;
-                        if (MODE == CS_TWO_POLY) {
-                            val_t z = MSK_COEF(fb + 1, k - 1);
-                            for (int i2 = k - 2; i2 >= 0; --i2)
-                                z = Ops::mul_add(z, xq, MSK_COEF(fb + 1, i2));
-                            g = Ops::canon(z);
-                        }
-                        u32 bucket, sb;
-                        split_row<F, NF>(h, g, mask, a.arb_r, bucket, sb);
-                        apply_update<PLACE>(tile, tile_saddr, a.counters, r, bucket, sb, cnt, false,
-                                            m, log2m, lcs);
-                    }
-                }
-            }
-        }
-        return;
-    }
+    if (PLACE == PLACE_GLOBAL) return;
 #undef MSK_COEF
     if (PLACE == PLACE_DSMEM)
         cluster_sync_all();  // every remote add into this block's slice has landed

@@ -37,7 +37,7 @@ using msi::cuda_fail;
 static const size_t kSmemTileBudget = 112 * 1024;
 static const int kMaxReplicas = 32;   // replicas a large sketch owns (<= 64 MiB)
 static const int kDefaultReplicas = 16;  // replicas a default launch uses
-static const int kHotLog2 = 12;          // hot-key table: 4096 slots (48 KiB) per block
+static const int kDedupLog2 = 12;        // de-duplication table: 4096 slots (48 KiB) per block
 
 namespace {
 
@@ -563,19 +563,21 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
     a.n = n;
     a.replicas = cfg.replicas ? sk->replicas : nullptr;
     a.replica_mask = cfg.replicas ? (u32)(cfg.replicas - 1) : 0u;
-    a.aggregate = ov.aggregate >= 0 ? ov.aggregate : 1;
-    // Hot-key table (unit weights, one-word keys, global placement): its 12
-    // bytes per slot follow the coefficients in shared memory.  Re-derived after
-    // every change of placement below, so cfg.smem always covers what the
-    // kernel will touch.
-    auto set_hot = [&](bool allow) {
+    a.aggregate = ov.aggregate >= 0 ? ov.aggregate : 2;
+    // De-duplication (unit weights, one-word keys, global placement): a table of
+    // 12-byte slots and a 12-byte-entry queue per warp follow the coefficients in
+    // shared memory.  Re-derived after every change of placement below, so
+    // cfg.smem always covers what the kernel will touch.
+    auto set_dedup = [&](bool allow) {
         const bool on = allow && unit_weights && a.aggregate >= 2 &&
                         cfg.place == msk::PLACE_GLOBAL && sk->prime != msk::PRIME_89;
-        a.hot_log2 = on ? kHotLog2 : 0;
+        a.dedup_log2 = on ? kDedupLog2 : 0;
         cfg.smem = (cfg.place == msk::PLACE_GLOBAL ? 0 : tile_bytes / cfg.cluster) + extra;
-        if (on) cfg.smem = (cfg.smem + 15) / 16 * 16 + ((size_t)12 << kHotLog2);
+        if (on)
+            cfg.smem = (cfg.smem + 15) / 16 * 16 + ((size_t)12 << kDedupLog2) +
+                       (size_t)(cfg.threads / 32) * msk::DEDUP_QCAP * 12;
     };
-    set_hot(true);
+    set_dedup(true);
 
     // resident capacity (the cluster query needs a grid that is a whole cluster)
     cfg.blocks = cfg.cluster;
@@ -592,7 +594,7 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
         a.cluster_log2 = 0;
         a.replicas = cfg.replicas ? sk->replicas : nullptr;
         a.replica_mask = cfg.replicas ? (u32)(cfg.replicas - 1) : 0u;
-        set_hot(true);
+        set_dedup(true);
         e = msk::query_cs_update_occupancy(sk->prime, a, sk->words.data(), cfg, &occ);
         if (e != cudaSuccess || occ < 1) return cuda_fail(e, "occupancy");
     }
@@ -636,7 +638,7 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
         a.cluster_log2 = 0;
         a.replicas = nullptr;
         a.replica_mask = 0;
-        set_hot(false);  // per-block counts could overflow int32 too
+        set_dedup(false);  // per-block counts could overflow int32 too
     }
     return MS_OK;
 }

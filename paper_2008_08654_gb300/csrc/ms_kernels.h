@@ -30,6 +30,9 @@ enum Strategy {
 };
 
 constexpr int MAX_T = 15;
+// De-duplication (PLACE_GLOBAL, unit weights): entries of each warp's queue of
+// keys waiting to be hashed (fewer than 128 wait, one chunk adds at most 128).
+constexpr u32 DEDUP_QCAP = 256;
 constexpr int MAX_K = 8;
 constexpr int MAX_COEF_WORDS = MAX_T * 2 * MAX_K * 2;  // t * functions * k * limbs
 
@@ -47,8 +50,8 @@ struct UpdateArgs {
                              // or NULL for direct int64 atomics
     u32 replica_mask;        // R - 1 (R a power of two)
     int aggregate;           // PLACE_GLOBAL, unit weights: merge equal keys of a warp
-    int hot_log2;            // PLACE_GLOBAL, unit weights: log2 slots of the per-block
-                             // hot-key table in shared memory (0 = none)
+    int dedup_log2;          // PLACE_GLOBAL, unit weights, one-word keys: log2 slots of
+                             // the per-block de-duplication table (0 = none)
     u32 arb_r;               // any number of buckets: r (rows are 2^log2m >= r wide);
                              // 0: power-of-two buckets (generic kernels only)
 };

@@ -1,0 +1,138 @@
+"""De-duplicating update (unit weights, global placement, one-word keys): a key
+held by the block's table is counted and hashed once with its count, the rest
+are hashed from per-warp queues.  A sketch is linear in the stream (Sec. 1.3),
+so the counters must equal the oracle's key-by-key update exactly, whatever the
+table absorbs: ragged queue drains, saturated and colliding tables, the table's
+EMPTY word as a key, every block size and grid, every mode and prime."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from test_gpu_parity import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2008_08654_gb300 as ms
+    assert torch.cuda.is_available()
+    ms.lib()
+    return torch, ms
+
+
+def zipf_keys(b, n, seed, ranks=1 << 20):
+    z = datagen.zipf(seed, 1.1, ranks, n)
+    if b == 31:
+        return (z & np.uint64(0x7FFFFFFF)).astype(np.uint32)
+    return z
+
+
+def sketch_and_check(torch, ms, b, c, t, m, k, mode, keys, seed, **launch):
+    sk = ms.Sketch(t=t, m=m, k=k, b=b, c=c, seed=seed, mode=mode)
+    sk.set_launch(place=launch.pop("place", 2), **launch)
+    sk.update(to_dev(torch, keys))
+    ll = sk.last_launch()
+    C = sk.counters().cpu().numpy()
+    want = oracle.cs_update(b, c, k, t, sk.m, mode, oracle.sketch_coeffs(b, c, k, t, mode, seed), keys)
+    assert np.array_equal(C, want), "counters differ (%d cells)" % int((C != want).sum())
+    return sk, ll, want
+
+
+# sizes around one warp chunk (128 keys), one block chunk and the table size
+SIZES = [1, 3, 127, 128, 129, 255, 2047, 2049, 4097, 65537, 300007]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_ragged_sizes(env, n):
+    torch, ms = env
+    keys = zipf_keys(61, n, 11 + n)
+    _, ll, _ = sketch_and_check(torch, ms, 61, 1, 7, 1 << 16, 4, 0, keys, 3)
+    assert ll["place"] == 2 and ll["replicas"] > 0
+
+
+@pytest.mark.parametrize("threads,blocks", [(32, 0), (32, 1), (64, 3), (256, 0), (512, 0),
+                                            (512, 1), (128, 7)])
+def test_block_shapes(env, threads, blocks):
+    """Queue length and table drain depend on the warps per block."""
+    torch, ms = env
+    keys = zipf_keys(61, 100003, 5)
+    _, ll, _ = sketch_and_check(torch, ms, 61, 1, 7, 1 << 15, 4, 0, keys, 9,
+                                threads=threads, blocks=blocks)
+    assert ll["threads"] == threads and (blocks == 0 or ll["blocks"] == blocks)
+
+
+def test_saturated_table_and_collisions(env):
+    """Many more distinct repeated keys than table slots (every slot taken
+    early by a cold key), plus the table's EMPTY word (all ones) repeated."""
+    torch, ms = env
+    n = 400009
+    rng = np.random.default_rng(7)
+    warm = datagen.u64_below(21, 0, 20000)           # 20000 keys, each ~10 times
+    keys = warm[rng.integers(0, warm.size, n)]
+    keys[rng.random(n) < 0.05] = np.uint64((1 << 64) - 1)
+    keys[:64] = np.uint64((1 << 64) - 1)
+    for blocks in (0, 1):
+        sketch_and_check(torch, ms, 61, 1, 5, 1 << 15, 4, 0, keys, 13, blocks=blocks)
+
+
+def test_all_equal_and_all_distinct(env):
+    torch, ms = env
+    same = np.full(70001, 12345678901, dtype=np.uint64)
+    sketch_and_check(torch, ms, 61, 1, 7, 1 << 15, 4, 0, same, 2)
+    distinct = datagen.u64_below(8, 0, 70001)
+    sketch_and_check(torch, ms, 61, 1, 7, 1 << 15, 4, 0, distinct, 2)
+
+
+CASES = [
+    # b, c, t, m, k, mode, strategy
+    (61, 1, 7, 1 << 16, 4, 0, 1),                      # power sum, two-for-one
+    (61, 1, 7, 1 << 16, 4, 0, 0),                      # Horner
+    (61, 1, 5, 1 << 15, 4, oracle.TWO_POLY, 1),        # two polynomials
+    (61, 1, 5, 50000, 4, oracle.ANY_R, 1),             # any m (Algorithm Mersenne-arb-r)
+    (61, 1, 3, 1 << 17, 2, 0, -1),                     # generic kernel (runtime t, k)
+    (61, 1, 9, 1 << 15, 5, oracle.TWO_POLY, -1),       # generic, two polynomials
+    (64, 59, 7, 1 << 15, 4, 0, -1),                    # 2^64 - 59
+    (64, 59, 5, 40000, 4, oracle.ANY_R | oracle.TWO_POLY, -1),
+    (31, 1, 7, 1 << 15, 4, 0, -1),                     # 32-bit keys
+    (31, 1, 3, 1 << 16, 2, oracle.TWO_POLY, -1),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "-".join(map(str, c)))
+def test_modes_and_primes(env, case):
+    torch, ms = env
+    b, c, t, m, k, mode, strategy = case
+    keys = zipf_keys(b, 150001, 40 + t + k)
+    sk, ll, want = sketch_and_check(torch, ms, b, c, t, m, k, mode, keys, 17 + t, strategy=strategy)
+    assert sk.f2() == oracle.f2_estimate(want)
+
+
+def test_repeated_updates_accumulate(env):
+    """Two updates into one sketch: each launch drains its own tables."""
+    torch, ms = env
+    keys = zipf_keys(61, 200003, 77)
+    sk = ms.Sketch(t=7, m=1 << 16, k=4, seed=4)
+    sk.update(to_dev(torch, keys[:123457]))
+    sk.update(to_dev(torch, keys[123457:]))
+    C = sk.counters().cpu().numpy()
+    want = oracle.cs_update(61, 1, 4, 7, 1 << 16, 0, oracle.sketch_coeffs(61, 1, 4, 7, 0, 4), keys)
+    assert np.array_equal(C, want)
+
+
+@pytest.mark.parametrize("aggregate", [0, 1, 2])
+def test_aggregation_levels_agree(env, aggregate):
+    """Off, warp merging only, and warp merging with the table: one result."""
+    torch, ms = env
+    keys = zipf_keys(61, 250007, 3)
+    sketch_and_check(torch, ms, 61, 1, 7, 1 << 16, 4, 0, keys, 6, aggregate=aggregate)
+
+
+def test_direct_int64_placement(env):
+    """Place 3 (int64 atomics, no replicas) also takes the table."""
+    torch, ms = env
+    keys = zipf_keys(61, 100003, 8)
+    _, ll, _ = sketch_and_check(torch, ms, 61, 1, 5, 1 << 14, 4, 0, keys, 8, place=3)
+    assert ll["place"] == 3
