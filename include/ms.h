@@ -326,11 +326,12 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  *  sketch owns; default 16),
  *  aggregate (0, 1 or 2, default 2; unit weights and place 2 or 3 only):
  *  1 = lanes of a warp holding the same key send one update carrying their
- *  count; 2 = also a per-block table of 4096 keys in shared memory (one-word
- *  keys: every prime but 2^89-1): a key the table holds is only counted and is
+ *  count; 2 = a per-block table of 4096 keys in shared memory (one-word keys:
+ *  every prime but 2^89-1): a key the table holds is only counted, and is
  *  hashed once, with its count, when the block ends; the other keys are hashed
- *  128 at a time from a per-warp queue.  The counters are identical for every
- *  setting (a sketch is linear in the stream).
+ *  128 at a time from a per-warp queue.  A warp whose table takes under 1/8 of
+ *  its keys over its 16th..31st chunk of 128 stops using it.  The counters are
+ *  identical for every setting (a sketch is linear in the stream).
  * Errors: INVALID_ARG.
  */
 ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int threads, int blocks,

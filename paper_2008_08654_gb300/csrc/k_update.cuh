@@ -516,10 +516,11 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
     const u32 lanes_below = (1u << lane) - 1u;
     u32 qn = 0;      // de-duplication: this warp's queue length (warp-uniform)
     int drain = -1;  // de-duplication: -1 while streaming, then the batch being drained
-    // The loop runs on the block's first key index, so every warp of a block
-    // takes the same number of iterations (warps and lanes past the end load
-    // weight-0 keys): warp-wide matching relies on it, and so does the drain of
-    // the de-duplication table, which starts with a block barrier.
+    // de-duplication stays on for this warp while the table absorbs keys: over
+    // the warp's chunks 16..31 it must take at least 1/8 of them (a stream
+    // without repeats turns it off once the table has filled)
+    bool dd_on = dd_log2 != 0;
+    u32 dd_chunk = 0, dd_missed = 0;
     for (u64 jb = (u64)blockIdx.x * blockDim.x * 4ull;;) {
         typename Ops::key_t key[4];
         int wt[4];
@@ -534,7 +535,7 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
             jb += stride;
             KeyIO<F>::load(a.keys, j, n, vec, key);
             load_weights4(a.weights, j, n, vec, wt);
-            if (PLACE == PLACE_GLOBAL && a.aggregate && a.weights == nullptr) {
+            if (PLACE == PLACE_GLOBAL && a.aggregate == 1 && a.weights == nullptr) {
                 // Unit weights: lanes of this warp holding the same key would add
                 // to the same t counters.  The lowest such lane takes the group's
                 // count; the others keep weight 0.
@@ -546,19 +547,26 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                 }
             }
             if constexpr (DEDUP_OK) {
-                if (dd_log2) {
-                    // the table counts what it can; the rest waits in the queue until
-                    // 128 keys (four a lane) are there to hash
+                if (dd_on) {
+                    // the table counts what it can; the rest waits in the queue
+                    // until 128 keys (four a lane) are there to hash
+                    u32 missed = 0;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const bool miss = wt[q] != 0 && !dedup_count(tk, tc, dd_log2, (u64)key[q], wt[q]);
                         const u32 mb = __ballot_sync(0xffffffffu, miss);
                         if (miss) {
-                            const u32 pos = qn + __popc(mb & lanes_below);
+                            const u32 pos = qn + missed + __popc(mb & lanes_below);
                             qk[pos] = (u64)key[q];
                             qc[pos] = wt[q];
                         }
-                        qn += __popc(mb);
+                        missed += __popc(mb);
+                    }
+                    qn += missed;
+                    if (dd_chunk < 32u) {
+                        ++dd_chunk;
+                        if (dd_chunk > 16u) dd_missed += missed;
+                        if (dd_chunk == 32u && dd_missed > 16u * 128u * 7u / 8u) dd_on = false;
                     }
                     if (qn < 128u) continue;
                     __syncwarp();

@@ -124,7 +124,7 @@ def test_repeated_updates_accumulate(env):
 
 @pytest.mark.parametrize("aggregate", [0, 1, 2])
 def test_aggregation_levels_agree(env, aggregate):
-    """Off, warp merging only, and warp merging with the table: one result."""
+    """Off, warp merging, and the de-duplication table: one result."""
     torch, ms = env
     keys = zipf_keys(61, 250007, 3)
     sketch_and_check(torch, ms, 61, 1, 7, 1 << 16, 4, 0, keys, 6, aggregate=aggregate)
@@ -136,3 +136,23 @@ def test_direct_int64_placement(env):
     keys = zipf_keys(61, 100003, 8)
     _, ll, _ = sketch_and_check(torch, ms, 61, 1, 5, 1 << 14, 4, 0, keys, 8, place=3)
     assert ll["place"] == 3
+
+
+@pytest.mark.parametrize("threads,blocks", [(32, 1), (64, 2), (512, 3)])
+def test_table_switches_off_and_stays_exact(env, threads, blocks):
+    """A warp whose table absorbs under 1/8 of its chunks 16..31 hashes the
+    rest of its keys directly; what the queue and table already hold is still
+    drained.  Streams: all distinct; distinct then heavy repeats; heavy
+    repeats then distinct."""
+    torch, ms = env
+    chunk = 128 * (threads // 32) * blocks       # keys one round of the grid takes
+    n = chunk * 80 + 77
+    distinct = datagen.u64_below(31, 0, n)
+    hot = datagen.u64_below(32, 0, 50)
+    rng = np.random.default_rng(5)
+    repeats = hot[rng.integers(0, hot.size, n)]
+    cut = chunk * 40
+    streams = [distinct, np.concatenate([distinct[:cut], repeats[cut:]]),
+               np.concatenate([repeats[:cut], distinct[cut:]])]
+    for keys in streams:
+        sketch_and_check(torch, ms, 61, 1, 7, 1 << 15, 4, 0, keys, 12, threads=threads, blocks=blocks)
