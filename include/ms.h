@@ -330,7 +330,7 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  *  every prime but 2^89-1): a key the table holds is only counted, and is
  *  hashed once, with its count, when the block ends; the other keys are hashed
  *  128 at a time from a per-warp queue.  A warp whose table takes under 1/8 of
- *  its keys over its 16th..31st chunk of 128 stops using it.  The counters are
+ *  the keys of its 17th to 32nd chunks of 128 stops using it.  The counters are
  *  identical for every setting (a sketch is linear in the stream).
  * Errors: INVALID_ARG.
  */

@@ -514,13 +514,17 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
     const u64 stride = (u64)gridDim.x * blockDim.x * 4ull;
     const u32 lane = threadIdx.x & 31u;
     const u32 lanes_below = (1u << lane) - 1u;
-    u32 qn = 0;      // de-duplication: this warp's queue length (warp-uniform)
     int drain = -1;  // de-duplication: -1 while streaming, then the batch being drained
-    // de-duplication stays on for this warp while the table absorbs keys: over
-    // the warp's chunks 16..31 it must take at least 1/8 of them (a stream
-    // without repeats turns it off once the table has filled)
-    bool dd_on = dd_log2 != 0;
-    u32 dd_chunk = 0, dd_missed = 0;
+    // De-duplication state of this warp (warp-uniform), packed in one word:
+    // bits 0..8 the queue length, 9..14 chunks seen (up to 32), 15..26 keys the
+    // table missed in chunks 16..31 (counting from 0), bit 31 set while the
+    // table is in use.  It stays in use if it absorbed at least 1/8 of those
+    // chunks' keys (a stream without repeats turns it off once it has filled).
+    u32 dd = dd_log2 != 0 ? 0x80000000u : 0u;
+    // The loop runs on the block's first key index, so every warp of a block
+    // takes the same number of iterations (warps and lanes past the end load
+    // weight-0 keys): warp-wide matching relies on it, and so does the drain of
+    // the de-duplication table, which starts with a block barrier.
     for (u64 jb = (u64)blockIdx.x * blockDim.x * 4ull;;) {
         typename Ops::key_t key[4];
         int wt[4];
@@ -547,9 +551,10 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                 }
             }
             if constexpr (DEDUP_OK) {
-                if (dd_on) {
+                if (dd >> 31) {
                     // the table counts what it can; the rest waits in the queue
                     // until 128 keys (four a lane) are there to hash
+                    const u32 qn = dd & 0x1FFu;
                     u32 missed = 0;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -562,19 +567,21 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                         }
                         missed += __popc(mb);
                     }
-                    qn += missed;
-                    if (dd_chunk < 32u) {
-                        ++dd_chunk;
-                        if (dd_chunk > 16u) dd_missed += missed;
-                        if (dd_chunk == 32u && dd_missed > 16u * 128u * 7u / 8u) dd_on = false;
+                    dd += missed;  // queue length
+                    const u32 chunk = (dd >> 9) & 0x3Fu;
+                    if (chunk < 32u) {
+                        dd += 1u << 9;
+                        if (chunk >= 16u) dd += missed << 15;
+                        if (chunk == 31u && ((dd >> 15) & 0xFFFu) > 16u * 128u * 7u / 8u) dd &= 0x7FFFFFFFu;
                     }
-                    if (qn < 128u) continue;
+                    if ((dd & 0x1FFu) < 128u) continue;
                     __syncwarp();
-                    qn -= 128u;
+                    dd -= 128u;
+                    const u32 top = dd & 0x1FFu;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        key[q] = (typename Ops::key_t)qk[qn + lane + 32u * q];
-                        wt[q] = qc[qn + lane + 32u * q];
+                        key[q] = (typename Ops::key_t)qk[top + lane + 32u * q];
+                        wt[q] = qc[top + lane + 32u * q];
                     }
                     __syncwarp();
                 }
@@ -583,6 +590,7 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
             // batch 0: what is left in this warp's queue; then the table, four
             // slots a thread per batch
             if (drain == 0) {
+                const u32 qn = dd & 0x1FFu;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const u32 e = lane + 32u * q;

@@ -37,6 +37,7 @@ using msi::cuda_fail;
 static const size_t kSmemTileBudget = 112 * 1024;
 static const int kMaxReplicas = 32;   // replicas a large sketch owns (<= 64 MiB)
 static const int kDefaultReplicas = 16;  // replicas a default launch uses
+static const int kDedupReplicas = 8;     // ... when the de-duplication table is on
 static const int kDedupLog2 = 12;        // de-duplication table: 4096 slots (48 KiB) per block
 
 namespace {
@@ -543,8 +544,13 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
     // 3% faster than 256 with 16 replicas)
     if (ov.threads <= 0 && place == msk::PLACE_GLOBAL) cfg.threads = 512;
     cfg.replicas = 0;
+    // With the de-duplication table (unit weights, one-word keys) the hottest
+    // keys reach the counters once per block, so fewer replicas suffice (8 vs
+    // 16 measured 2% faster on the 2^28-key Zipf sketch, with half the reduce).
+    const int aggregate = ov.aggregate >= 0 ? ov.aggregate : 2;
+    const bool dedup_wanted = unit_weights && aggregate >= 2 && sk->prime != msk::PRIME_89;
     if (place == msk::PLACE_GLOBAL && !direct && sk->nrep > 0) {
-        int r = ov.replicas > 0 ? ov.replicas : kDefaultReplicas;
+        int r = ov.replicas > 0 ? ov.replicas : (dedup_wanted ? kDedupReplicas : kDefaultReplicas);
         if (r > sk->nrep) r = sk->nrep;
         cfg.replicas = r;
     }
@@ -563,14 +569,13 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
     a.n = n;
     a.replicas = cfg.replicas ? sk->replicas : nullptr;
     a.replica_mask = cfg.replicas ? (u32)(cfg.replicas - 1) : 0u;
-    a.aggregate = ov.aggregate >= 0 ? ov.aggregate : 2;
+    a.aggregate = aggregate;
     // De-duplication (unit weights, one-word keys, global placement): a table of
     // 12-byte slots and a 12-byte-entry queue per warp follow the coefficients in
     // shared memory.  Re-derived after every change of placement below, so
     // cfg.smem always covers what the kernel will touch.
     auto set_dedup = [&](bool allow) {
-        const bool on = allow && unit_weights && a.aggregate >= 2 &&
-                        cfg.place == msk::PLACE_GLOBAL && sk->prime != msk::PRIME_89;
+        const bool on = allow && dedup_wanted && cfg.place == msk::PLACE_GLOBAL;
         a.dedup_log2 = on ? kDedupLog2 : 0;
         cfg.smem = (cfg.place == msk::PLACE_GLOBAL ? 0 : tile_bytes / cfg.cluster) + extra;
         if (on)
@@ -640,6 +645,8 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
         a.replica_mask = 0;
         set_dedup(false);  // per-block counts could overflow int32 too
     }
+    // the table's int32 counts hold at most the keys one block sees
+    if (a.dedup_log2 && iters * per_iter >= 0x7FFFFFFFull) set_dedup(false);
     return MS_OK;
 }
 

@@ -140,8 +140,8 @@ def test_direct_int64_placement(env):
 
 @pytest.mark.parametrize("threads,blocks", [(32, 1), (64, 2), (512, 3)])
 def test_table_switches_off_and_stays_exact(env, threads, blocks):
-    """A warp whose table absorbs under 1/8 of its chunks 16..31 hashes the
-    rest of its keys directly; what the queue and table already hold is still
+    """A warp whose table absorbs under 1/8 of the keys of its 17th to 32nd
+    chunks hashes the rest of its keys directly; what the queue and table already hold is still
     drained.  Streams: all distinct; distinct then heavy repeats; heavy
     repeats then distinct."""
     torch, ms = env
