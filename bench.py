@@ -65,6 +65,7 @@ WORKLOADS = {
 # configuration; the stream's traffic grows in proportion, so a launch's traffic
 # is this times its keys.  Only workloads whose current kernel was captured.
 MEASURED_TRAFFIC_PER_KEY = {
+    "large": (283.238656e6 + 4.107008e6) / 2 ** 25,
     "plain-2^28": (402.737920e6 + 2.999296e6) / 2 ** 25,
 }
 
@@ -291,6 +292,22 @@ def run_ours(args, wl):
     # denominator) and 32x32->64 multiply-adds (context)
     mul_rate, _ = ms.probe_mul128(variant=0, iters=1 << 12)
     imad_rate, _ = ms.probe_mul128(variant=1, iters=1 << 13)
+    # entries one launch hashes (keys, or with the de-duplication table the
+    # distinct (block, key) entries): one untimed update with the stats hook on
+    hashed_t = torch.zeros(1, dtype=torch.int64, device=dev)
+    sk.set_stats(hashed_t)
+    sk.reset()
+    sk.update(keys, w)
+    torch.cuda.synchronize()
+    sk.set_stats(None)
+    hashed = int(hashed_t.item())
+    global_counters = launch.get("place") in (2, 3)
+    red_rate = None
+    if global_counters:
+        # scattered int32 atomic additions into an L2-resident buffer the size
+        # of the replicas (the counter updates' own bound)
+        words = 1 << max(5, ((max(1, launch.get("replicas") or 1) * t * m) - 1).bit_length())
+        red_rate, _ = ms.probe_red(words=words, iters=512)
 
     if rank != 0:
         if world > 1:
@@ -300,7 +317,8 @@ def run_ours(args, wl):
     value = world * n * args.steps / (ms_total * 1e-3)
     kern_avg_s = statistics.mean(kern_ms) * 1e-3
     mul128_per_key = t * 3 * (2 if mode == 1 else 1)
-    achieved_mul = n * mul128_per_key / kern_avg_s
+    # the integer work the launch executes: t(k-1) (or 2t(k-1)) mul128 per hashed entry
+    achieved_mul = hashed * mul128_per_key / kern_avg_s
     peak_mul = mul_rate
     bytes_per_key = 8 + (4 if w is not None else 0)
     hbm_peak = 6787.9
@@ -308,6 +326,46 @@ def run_ours(args, wl):
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except (OSError, KeyError, ValueError):
         pass
+    alu = {
+        "achieved": achieved_mul / 1e9,
+        "peak": peak_mul / 1e9,
+        "unit": "Gmul128/s",
+        "frac": achieved_mul / peak_mul,
+        "mul128_per_hashed_entry": mul128_per_key,
+        "peak_source": "ms_probe_mul128 variant 0: independent 64x64->128 products "
+                       "(low half by multiplication, high half by __umul64hi), 8 chains per "
+                       "thread on every SM, measured in this run",
+        "probe_mad_wide_32x32_per_s": imad_rate,
+    }
+    if global_counters:
+        adds = hashed * t / kern_avg_s  # counter additions (one per row per hashed entry)
+        roofline = {
+            "bound": "l2_atomic",
+            "achieved": adds / 1e9,
+            "peak": red_rate / 1e9,
+            "unit": "Gadd/s",
+            "frac": adds / red_rate,
+            "peak_source": "ms_probe_red: scattered red.global.add.s32 into an L2-resident "
+                           "buffer the size of the replicas, every SM, measured in this run",
+            "alu": alu,
+        }
+    else:
+        roofline = {"bound": "alu"}
+        roofline.update({k: alu[k] for k in ("achieved", "peak", "unit", "frac")})
+        roofline.update({k: alu[k] for k in ("mul128_per_hashed_entry", "peak_source",
+                                             "probe_mad_wide_32x32_per_s")})
+    roofline.update({
+        "traffic": (MEASURED_TRAFFIC_PER_KEY[args.workload] * n
+                    if args.workload in MEASURED_TRAFFIC_PER_KEY else None),
+        "traffic_unit": "bytes per launch (ncu DRAM bytes of a 2^25-key capture, scaled)",
+        "algorithmic_bytes": n * bytes_per_key,
+        "kernel": "k_cs_update",
+        "kernel_ms": statistics.mean(kern_ms),
+        "keys_per_launch": n,
+        "hashed_entries_per_launch": hashed,
+        "hbm": {"achieved_gbs": n * bytes_per_key / kern_avg_s / 1e9, "peak_gbs": hbm_peak,
+                "frac": n * bytes_per_key / kern_avg_s / 1e9 / hbm_peak},
+    })
     line = {
         "metric": "Count Sketch key updates/s (k=4, p=2^61-1)",
         "value": value,
@@ -327,26 +385,7 @@ def run_ours(args, wl):
                    "l2": "inputs (%d MiB per GPU) exceed the 129 MB L2; no flush" %
                          (n * bytes_per_key >> 20),
                    "launch": launch, "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {
-            "bound": "alu",
-            "achieved": achieved_mul / 1e9,
-            "peak": peak_mul / 1e9,
-            "unit": "Gmul128/s",
-            "frac": achieved_mul / peak_mul,
-            "traffic": (MEASURED_TRAFFIC_PER_KEY[args.workload] * n
-                        if args.workload in MEASURED_TRAFFIC_PER_KEY else None),
-            "traffic_unit": "bytes per launch (ncu DRAM bytes of a 2^25-key capture, scaled)",
-            "algorithmic_bytes": n * bytes_per_key,
-            "kernel": "k_cs_update",
-            "kernel_ms": statistics.mean(kern_ms),
-            "mul128_per_key": mul128_per_key,
-            "peak_source": "ms_probe_mul128 variant 0: independent 64x64->128 products "
-                           "(low half by multiplication, high half by __umul64hi), 8 chains per "
-                           "thread on every SM, measured in this run",
-            "probe_mad_wide_32x32_per_s": imad_rate,
-            "hbm": {"achieved_gbs": n * bytes_per_key / kern_avg_s / 1e9, "peak_gbs": hbm_peak,
-                    "frac": n * bytes_per_key / kern_avg_s / 1e9 / hbm_peak},
-        },
+        "roofline": roofline,
         "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": "keys/s",
                 "h2d_bytes_per_step": n * bytes_per_key, "d2h_bytes_per_step": 16},
         # zero, update, (replica reduce,) F2 per timed step

@@ -337,13 +337,25 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
 ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int threads, int blocks,
                         int blocks_per_sm, int cluster, int replicas, int aggregate);
 
+/*
+ * cs_set_stats -- measurement hook (not in the paper): while `hashed_dev` (a
+ * device uint64, 8-byte aligned) is set, every cs_update / cs_update_host on
+ * this sketch atomically adds to it the number of entries it hashed with a
+ * non-zero count: the keys with a non-zero weight, or with the
+ * de-duplication table the distinct (block, key) entries it counted.  Each
+ * hashed entry costs t polynomial evaluations and t counter additions.  It adds
+ * one atomic per warp per 128 entries.  NULL turns it off.
+ * Errors: INVALID_ARG, MISALIGNED.
+ */
+ms_status cs_set_stats(cs_sketch* sk, uint64_t* hashed_dev);
+
 /* The configuration the most recent cs_update on this sketch launched with;
  * `specialized` is 1 when a compile-time (t, k) kernel served it.  Any output
  * pointer may be NULL. */
 ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* threads, int* blocks,
                          int* cluster, int* smem, int* specialized, int* replicas);
 
-/* ---------------------------------------------------- integer-pipe peak probe */
+/* ---------------------------------------------------- peak probes */
 
 /*
  * ms_probe_mul128 -- measures this GPU's throughput of independent integer
@@ -361,6 +373,18 @@ ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* th
  *  variant 3: one 32-bit integer add (two dependent adds per step, both counted).
  */
 ms_status ms_probe_mul128(int variant, int iters, uint64_t* sink_dev, double* rate, double* ms);
+
+/*
+ * ms_probe_red -- measures the throughput of scattered 32-bit atomic additions
+ * (red.global.add.s32) into `buf_dev` (`words` int32, a power of two from 32 to
+ * 2^31): every thread of a full-occupancy grid adds 1 to 4 * `iters`
+ * pseudo-random words.  A buffer the size of the update's replica counters
+ * stays in L2, so the rate is the L2's atomic throughput, the unit the global
+ * placement's counter updates are bounded by.  Writes additions/s to *rate and
+ * the kernel time to *ms; the buffer's words are incremented.  Synchronous.
+ * Errors: INVALID_ARG, MISALIGNED, CUDA.
+ */
+ms_status ms_probe_red(int32_t* buf_dev, size_t words, int iters, double* rate, double* ms);
 
 #ifdef __cplusplus
 }

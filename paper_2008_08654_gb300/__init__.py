@@ -6,7 +6,8 @@ CUDA kernels.  PyTorch supplies device memory and streams.  There is no CPU
 fallback: if libms.so is missing or a call fails, an exception is raised.
 
 Names follow the C ABI: hash_init / Hash.eval (ms_hash_*), div / mod
-(ms_div / ms_mod), Sketch (cs_*), probe_mul128 (ms_probe_mul128).
+(ms_div / ms_mod), Sketch (cs_*), probe_mul128 (ms_probe_mul128), probe_red
+(ms_probe_red).
 """
 from __future__ import annotations
 
@@ -94,6 +95,8 @@ def _load():
         "cs_set_launch": (i, [vp, i, i, i, i, i, i, i, i]),
         "cs_last_launch": (i, [vp, ip, ip, ip, ip, ip, ip, ip, ip]),
         "ms_probe_mul128": (i, [i, i, vp, dbl, dbl]),
+        "ms_probe_red": (i, [vp, sz, i, dbl, dbl]),
+        "cs_set_stats": (i, [vp, vp]),
         "cs_batch_default_tuning": (i, [vp]),
         "cs_batch_create": (i, [pp, vp, i, vp, vp]),
         "cs_batch_launch": (i, [vp, vp]),
@@ -416,6 +419,16 @@ class Sketch:
         _check(_load().cs_set_launch(self._h, place, strategy, threads, blocks, blocks_per_sm,
                                      cluster, replicas, aggregate), "cs_set_launch")
 
+    def set_stats(self, hashed=None):
+        """Measurement hook: later updates add the entries they hash (t polynomial
+        evaluations and t counter additions each) into `hashed`, a one-element
+        int64 CUDA tensor; None turns it off."""
+        if hashed is not None and (hashed.dtype != torch.int64 or hashed.numel() < 1):
+            raise ValueError("hashed must be a one-element int64 CUDA tensor")
+        _check(_load().cs_set_stats(self._h, None if hashed is None else _ptr(hashed)),
+               "cs_set_stats")
+        self._stats = hashed  # keep the counter alive while the library holds it
+
     def last_launch(self) -> dict:
         v = [ctypes.c_int() for _ in range(8)]
         _check(_load().cs_last_launch(self._h, *[ctypes.byref(x) for x in v]), "cs_last_launch")
@@ -442,6 +455,16 @@ def probe_mul128(variant: int = 0, iters: int = 4096) -> tuple:
     rate, ms = ctypes.c_double(), ctypes.c_double()
     _check(_load().ms_probe_mul128(variant, iters, _ptr(sink), ctypes.byref(rate),
                                    ctypes.byref(ms)), "ms_probe_mul128")
+    return rate.value, ms.value
+
+
+def probe_red(words: int = 1 << 22, iters: int = 256) -> tuple:
+    """(scattered int32 atomic additions per second, kernel ms) into a buffer of
+    `words` int32 (4 * 2^22 bytes = 16 MiB by default, L2-resident)."""
+    buf = torch.zeros(words, dtype=torch.int32, device="cuda")
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_load().ms_probe_red(_ptr(buf), words, iters, ctypes.byref(rate), ctypes.byref(ms)),
+           "ms_probe_red")
     return rate.value, ms.value
 
 

@@ -487,4 +487,53 @@ cudaError_t run_probe_mul128(int variant, int iters, u64* sink, double* rate, do
     return cudaSuccess;
 }
 
+// L2 atomic throughput: every thread adds 1 to `iters` pseudo-random words of
+// buf (words a power of two), four independent additions in flight per step.
+// Sized like the update's int32 replicas, the buffer stays in L2, so the rate
+// is that of the L2's atomic units for scattered 32-bit reductions.
+__global__ void __launch_bounds__(256) k_probe_red(int* buf, u32 mask, int iters, u32 seed) {
+    const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
+    u32 base = (tid * 0x9E3779B1u) ^ seed;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            u32 h = (base + (u32)c) * 0x85EBCA6Bu;
+            h ^= h >> 13;
+            atomicAdd(buf + (h & mask), 1);
+        }
+        base += 0x632BE5ABu;
+    }
+}
+
+cudaError_t run_probe_red(int* buf, u64 words, int iters, double* rate, double* ms) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_red, 256, 0);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * (per_sm > 0 ? per_sm : 1);
+    const u32 mask = (u32)(words - 1);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_probe_red<<<blocks, 256>>>(buf, mask, iters / 8 + 1, 0x1234567u);  // warm-up
+    cudaEventRecord(e0);
+    k_probe_red<<<blocks, 256>>>(buf, mask, iters, 0x7654321u);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *ms = t;
+    *rate = (double)blocks * 256.0 * 4.0 * (double)iters / (t * 1e-3);
+    return cudaSuccess;
+}
+
 }  // namespace msk

@@ -612,6 +612,12 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
         } else {
             break;
         }
+        if (a.hashed) {  // measurement: entries about to be hashed with a non-zero count
+            u32 c = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c += __popc(__ballot_sync(0xffffffffu, wt[q] != 0));
+            if (lane == 0 && c) atomicAdd(a.hashed, (unsigned long long)c);
+        }
         bool big[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {

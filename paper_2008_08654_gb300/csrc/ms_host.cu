@@ -563,6 +563,7 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
     a.log2m = sk->log2m;
     a.mode = sk->mode & CS_TWO_POLY;
     a.arb_r = sk->r;
+    a.hashed = sk->hashed;
     a.cluster_log2 = lcs;
     a.coef_dev = sk->coef_dev;
     a.counters = sk->counters;
@@ -910,6 +911,15 @@ extern "C" ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int t
     return MS_OK;
 }
 
+// Measurement hook: later cs_update calls add the entries they hash into
+// *hashed_dev (NULL turns it off).
+extern "C" ms_status cs_set_stats(cs_sketch* sk, uint64_t* hashed_dev) {
+    if (!sk) return MS_ERR_INVALID_ARG;
+    if (hashed_dev && !aligned(hashed_dev, 8)) return MS_ERR_MISALIGNED;
+    sk->hashed = (unsigned long long*)hashed_dev;
+    return MS_OK;
+}
+
 // The configuration the last cs_update on this sketch launched with.
 extern "C" ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* threads,
                                     int* blocks, int* cluster, int* smem, int* specialized,
@@ -935,5 +945,15 @@ extern "C" ms_status ms_probe_mul128(int variant, int iters, uint64_t* sink_dev,
     if (!sink_dev || !rate || !ms || iters < 1 || variant < 0 || variant > 3)
         return MS_ERR_INVALID_ARG;
     MS_CUDA(msk::run_probe_mul128(variant, iters, (u64*)sink_dev, rate, ms), "ms_probe_mul128");
+    return MS_OK;
+}
+
+extern "C" ms_status ms_probe_red(int32_t* buf_dev, size_t words, int iters, double* rate,
+                                  double* ms) {
+    if (!buf_dev || !rate || !ms || iters < 1 || words < 32 || words > (1ull << 31) ||
+        (words & (words - 1)) != 0)
+        return MS_ERR_INVALID_ARG;
+    if (!aligned(buf_dev, 4)) return MS_ERR_MISALIGNED;
+    MS_CUDA(msk::run_probe_red((int*)buf_dev, (u64)words, iters, rate, ms), "ms_probe_red");
     return MS_OK;
 }

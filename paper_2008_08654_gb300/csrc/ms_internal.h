@@ -41,6 +41,7 @@ struct cs_sketch {
     cudaEvent_t hcopied[2] = {nullptr, nullptr};
     cudaEvent_t hfree[2] = {nullptr, nullptr};
     LaunchOverride launch;
+    unsigned long long* hashed = nullptr;  // cs_set_stats: device counter of hashed entries
     msk::LaunchCfg last_cfg = {};
     int last_specialized = 0;
 };

@@ -54,6 +54,7 @@ struct UpdateArgs {
                              // the per-block de-duplication table (0 = none)
     u32 arb_r;               // any number of buckets: r (rows are 2^log2m >= r wide);
                              // 0: power-of-two buckets (generic kernels only)
+    unsigned long long* hashed;  // optional: += entries hashed with a non-zero count
 };
 
 // Whether cs_update runs a compile-time (t, k) kernel (coefficients in the
@@ -137,5 +138,6 @@ cudaError_t launch_divmod(int prime, const ms_u128* v, ms_u128* q, void* r, u64 
                           cudaStream_t stream);
 
 cudaError_t run_probe_mul128(int variant, int iters, u64* sink, double* rate, double* ms);
+cudaError_t run_probe_red(int* buf, u64 words, int iters, double* rate, double* ms);
 
 }  // namespace msk

@@ -140,3 +140,21 @@ def test_hash_eval_rejects_bad_pointers_before_launch(ms):
     assert lib.ms_hash_eval(h._h, None, None, 10, None) == 1
     assert lib.ms_hash_eval(h._h, None, None, 0, None) == 0
     assert lib.ms_hash_eval(h._h, ctypes.c_void_p(0x1003), ctypes.c_void_p(0x2000), 10, None) == 8
+
+
+def test_probes_and_stats_hook_validate_on_the_host(ms):
+    """The peak probes and the measurement hook reject bad arguments before
+    touching a device."""
+    lib = ms.lib()
+    r, t = ctypes.c_double(), ctypes.c_double()
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails validation
+    assert lib.ms_probe_red(None, 1 << 20, 4, ctypes.byref(r), ctypes.byref(t)) == 1
+    assert lib.ms_probe_red(fake, 1000, 4, ctypes.byref(r), ctypes.byref(t)) == 1   # not 2^j
+    assert lib.ms_probe_red(fake, 16, 4, ctypes.byref(r), ctypes.byref(t)) == 1     # too small
+    assert lib.ms_probe_red(fake, 1 << 32, 4, ctypes.byref(r), ctypes.byref(t)) == 1
+    assert lib.ms_probe_red(fake, 1 << 20, 0, ctypes.byref(r), ctypes.byref(t)) == 1
+    assert lib.ms_probe_red(fake, 1 << 20, 4, None, ctypes.byref(t)) == 1
+    assert lib.ms_probe_red(ctypes.c_void_p((1 << 20) + 2), 1 << 20, 4, ctypes.byref(r),
+                            ctypes.byref(t)) == 8                                   # misaligned
+    assert lib.ms_probe_mul128(4, 16, fake, ctypes.byref(r), ctypes.byref(t)) == 1  # variant
+    assert lib.cs_set_stats(None, None) == 1
