@@ -154,12 +154,20 @@ __device__ __forceinline__ void split_row(const typename FieldOps<F>::val_t& h,
 // constant offset, so the multiply instructions read them straight from the
 // constant bank.  For p = 2^61-1 the 31-bit splits used by the power-sum
 // evaluation are precomputed on the host.
+// For 2^89-1 and 2^64-59 the power sum also takes 18 precomputed limbs per
+// function (k = 4), built by fill_param_coef.
+template <class F>
+struct PsLimbs {
+    static constexpr int N = (std::is_same<F, msf::P89>::value || std::is_same<F, msf::P64>::value) ? 18 : 0;
+};
+
 template <class F, int NFUN, int K>
 struct ParamCoef {
     u64 w[NFUN > 0 ? NFUN * K * FieldOps<F>::WORDS : 1];
     u32 lo[NFUN > 0 ? NFUN * K : 1];  // P61 only: a & (2^31-1)
     u32 hi[NFUN > 0 ? NFUN * K : 1];  // P61 only: a >> 31
     int nd[NFUN > 0 ? NFUN * K : 1];  // P61 only: lo - hi
+    u32 ps[(NFUN > 0 && K == 4 && PsLimbs<F>::N > 0) ? NFUN * PsLimbs<F>::N : 1];  // P89, P64
     u32 c2p31, c4;                    // 2^31 and 4, as run-time operands
 };
 
@@ -411,6 +419,33 @@ __device__ __forceinline__ void p61_row_bs(const msf::P61::Pow3& xp, const PC& p
         u32 unused;
         F::row_kara(xp, sl, sh, sn, pc.w[fs * 4], pc.c2p31, pc.c4, ylo, yhi);
         F::bucket_sign_hl(ylo, yhi, mask, unused, sign);
+    }
+}
+
+// Bucket and sign bit of row r for p = 2^31-1, 2^89-1, 2^64-59 and k = 4 (power
+// sum of the prime's field policy), two-for-one or two polynomials.
+template <class F, int NF, class PC>
+__device__ __forceinline__ void ps_row_bs(const typename F::Pow3& xp, const PC& pc, int r, u32 mask,
+                                          u32& bucket, u32& sign) {
+    const int fb = r * NF;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+        const int f = fb + j;
+        u32 b, s;
+        if constexpr (std::is_same<F, msf::P31>::value) {
+            F::row_bs(xp, (u32)pc.w[f * 4], (u32)pc.w[f * 4 + 1], (u32)pc.w[f * 4 + 2],
+                      (u32)pc.w[f * 4 + 3], mask, b, s);
+        } else {
+            u32 c[18];
+#pragma unroll
+            for (int i = 0; i < 18; ++i) c[i] = pc.ps[f * 18 + i];
+            if constexpr (std::is_same<F, msf::P64>::value)
+                F::row_bs(xp, pc.w[f * 4], c, mask, b, s);
+            else
+                F::row_bs(xp, c, mask, b, s);
+        }
+        if (j == 0) bucket = b;
+        sign = s;  // two polynomials: the second one's bit b-1
     }
 }
 
@@ -675,6 +710,47 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                         } else {
                             apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket, d, log2m, lcs);
                         }
+                    }
+                }
+            }
+        } else if constexpr (!GENERIC && STRAT >= STRAT_POWER_SUM && K == 4 &&
+                             !std::is_same<F, msf::P61>::value) {
+            // the other primes' power sum: keys outer, one key's powers live
+            // at a time, in every placement
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (big[q]) {
+                    update_big_key<F, NF>(Ops::prep(key[q]), wt[q], a.coef_dev, t, k, log2m,
+                                          a.arb_r, a.counters);
+                    wt[q] = 0;
+                }
+            }
+            // A rolled loop over the four keys (the key registers rotate, so no
+            // array is indexed at run time): unrolled, the compiler interleaves
+            // the keys and runs out of registers.
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                typename F::Pow3 xp;
+                F::powers3(key[0], xp);
+                const int w = wt[0], w2 = -2 * w;
+                key[0] = key[1];
+                key[1] = key[2];
+                key[2] = key[3];
+                wt[0] = wt[1];
+                wt[1] = wt[2];
+                wt[2] = wt[3];
+                u32 rbase = tile_saddr;  // shared address of row r's counters
+#pragma unroll
+                for (int r = 0; r < T; ++r) {
+                    u32 bucket, sb;
+                    ps_row_bs<F, NF>(xp, pc, r, mask, bucket, sb);
+                    const int d = (int)sb * w2 + w;
+                    if (PLACE == PLACE_SMEM) {
+                        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(rbase + (bucket << 2)), "r"(d)
+                                     : "memory");
+                        rbase += row_bytes;
+                    } else {
+                        apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket, d, log2m, lcs);
                     }
                 }
             }

@@ -30,6 +30,35 @@ static void fill_param_coef(ParamCoef<F, NFUN, K>& pc, const u64* words) {
         pc.hi[i] = (u32)(a >> 31);
         pc.nd[i] = (int)pc.lo[i] - (int)pc.hi[i];
     }
+    if constexpr (K == 4 && PsLimbs<F>::N > 0) {
+        for (int f = 0; f < NFUN; ++f) {
+            u32* c = pc.ps + f * 18;
+            const u64* a = words + (size_t)f * K * W;
+            if constexpr (std::is_same<F, msf::P89>::value) {
+                // a0's 30-bit limbs, then (l0, l1, l2, 2 l1, 2 l2) of a1, a2, a3
+                for (int i = 0; i < 4; ++i) {
+                    const unsigned __int128 v = ((unsigned __int128)a[2 * i + 1] << 64) | a[2 * i];
+                    const u32 l0 = (u32)(v & 0x3FFFFFFFu), l1 = (u32)((v >> 30) & 0x3FFFFFFFu);
+                    const u32 l2 = (u32)(v >> 60);
+                    if (i == 0) {
+                        c[0] = l0; c[1] = l1; c[2] = l2;
+                    } else {
+                        u32* d = c + 3 + 5 * (i - 1);
+                        d[0] = l0; d[1] = l1; d[2] = l2; d[3] = 2 * l1; d[4] = 2 * l2;
+                    }
+                }
+            } else {
+                // b_iv = a_i 2^(29 v) mod (2^64 - 59), low and high halves
+                const unsigned __int128 p = (((unsigned __int128)1) << 64) - 59;
+                for (int i = 1; i < 4; ++i)
+                    for (int v = 0; v < 3; ++v) {
+                        const u64 b = (u64)((((unsigned __int128)a[i]) << (29 * v)) % p);
+                        c[6 * (i - 1) + 2 * v] = (u32)b;
+                        c[6 * (i - 1) + 2 * v + 1] = (u32)(b >> 32);
+                    }
+            }
+        }
+    }
 }
 
 template <class F, int T, int K, int MODE, int PLACE, int STRAT>
@@ -80,10 +109,13 @@ static cudaError_t launch_exact(const UpdateArgs& a, const u64* coef_host, const
 template <class F, int T, int K, int MODE, int PLACE>
 static cudaError_t launch_strat(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
                                 cudaStream_t stream, int* occupancy) {
-    constexpr bool PS_OK = std::is_same<F, msf::P61>::value && K == 4;
+    // the power sum: every prime at k = 4; the any-m map only for 2^61-1 (the
+    // other primes' any-m sketches take the generic kernel)
+    constexpr bool PS_OK = K == 4;
+    constexpr bool ANY_OK = std::is_same<F, msf::P61>::value && K == 4;
     if (PS_OK && cfg.strategy == STRAT_POWER_SUM) {
         if (a.arb_r)
-            return launch_exact<F, T, K, MODE, PLACE, PS_OK ? STRAT_POWER_SUM_ANY_R : STRAT_HORNER>(
+            return launch_exact<F, T, K, MODE, PLACE, ANY_OK ? STRAT_POWER_SUM_ANY_R : STRAT_HORNER>(
                 a, coef_host, cfg, stream, occupancy);
         return launch_exact<F, T, K, MODE, PLACE, PS_OK ? STRAT_POWER_SUM : STRAT_HORNER>(
             a, coef_host, cfg, stream, occupancy);

@@ -30,6 +30,13 @@ struct u128x {  // a two-limb key/value as it sits in memory
     u64 lo, hi;
 };
 
+// 32x32 -> 64-bit multiply-add, a * b + c (one wide integer multiply-add).
+__device__ __forceinline__ u64 madw(u32 a, u32 b, u64 c) {
+    u64 d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
 // ---------------------------------------------------------------- p = 2^61-1
 //
 // Elements are split into a 31-bit low part and a high part,
@@ -98,13 +105,6 @@ struct P61 {
         const u64 j = hx & ((1ull << 60) - 1);
         bucket = (u32)((__umul64hi(j, (u64)r) << 4) | ((j * (u64)r) >> 60));
         a = (u32)(hx >> 60);
-    }
-
-    // 32x32 -> 64-bit multiply-add, a * b + c (one wide integer multiply-add).
-    __device__ static __forceinline__ u64 madw(u32 a, u32 b, u64 c) {
-        u64 d;
-        asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-        return d;
     }
 
     // ---- Karatsuba power sum (the update kernels' row hash) ----
@@ -255,6 +255,38 @@ struct P31 {
     __device__ static __forceinline__ u32 bucket(u32 h, u32 mask) { return h & mask; }
     __device__ static __forceinline__ u32 sign_bit(u32 h) { return (h >> 30) & 1u; }
 
+    // ---- power sum (the update kernels' row hash for k = 4) ----
+    //
+    // x canonical, x^2 and x^3 lazy (< 2^31 + 3, from mul_add).
+    struct Pow3 {
+        u32 x[3];
+    };
+
+    __device__ static __forceinline__ void powers3(u32 key, Pow3& xp) {
+        const u32 x = reduce_key(key);
+        xp.x[0] = x;
+        xp.x[1] = mul_add(x, x, 0u);
+        xp.x[2] = mul_add(xp.x[1], x, 0u);
+    }
+
+    // Bucket and sign bit of y = a0 + a1 x + a2 x^2 + a3 x^3 (mod p), all a_i < p:
+    //   S = a1 x + a2 x^2 + a3 x^3 + a0 < 3 2^31 (2^31 + 3) + 2^31 < 2^64
+    //   2^32 = 2 (mod p):  v = 2 S.hi + S.lo < 3 2^32
+    //   f = (v & p) + (v >> 31) < 2^31 + 6 < 2p
+    // f >= p exactly when f + 1 >= 2^31; then the residue f - p = f + 1 - 2^31
+    // is below 8 (bit 30 clear) and has the low bits of f + 1.
+    __device__ static __forceinline__ void row_bs(const Pow3& xp, u32 a0, u32 a1, u32 a2, u32 a3,
+                                                  u32 mask, u32& bucket, u32& sign) {
+        u64 S = madw(a1, xp.x[0], (u64)a0);
+        S = madw(a2, xp.x[1], S);
+        S = madw(a3, xp.x[2], S);
+        const u64 v = madw((u32)(S >> 32), 2u, S & 0xFFFFFFFFull);
+        const u32 f = ((u32)v & P) + (u32)(v >> 31);
+        const u32 over = (f + 1u) >> 31;
+        bucket = (f + over) & mask;
+        sign = over ? 0u : ((f >> 30) & 1u);
+    }
+
     // Algorithm Mersenne-arb-r (Sec. 3.3): h' = h + 1, bucket floor(r j / 2^30)
     // for its low 30 bits j, a = its top bit.
     __device__ static __forceinline__ void arb_split(u32 h, u32 r, u32& bucket, u32& a) {
@@ -312,6 +344,106 @@ struct P89 {
     __device__ static __forceinline__ u32 bucket(u128 h, u32 mask) { return (u32)h & mask; }
     __device__ static __forceinline__ u32 sign_bit(u128 h) { return (u32)(h >> 88) & 1u; }
 
+    // ---- power sum with 30-bit limbs (the update kernels' row hash, k = 4) ----
+    //
+    // A value is z = z0 + z1 2^30 + z2 2^60 with z0, z1 < 2^30 and z2 <= 2^29
+    // (so z < 2^90; lazy, not necessarily below p).  Since 2^89 = 1 (mod p),
+    //   2^90 = 2  and  2^120 = 2^31 = 2 * 2^30  (mod p),
+    // so the columns 3 and 4 of a 3-limb product wrap onto columns 0 and 1
+    // with a factor 2, and every product of two values is
+    //   L0 + L1 2^30 + L2 2^60  with
+    //   L0 = y0 z0 + y1 (2 z2) + y2 (2 z1),  L1 = y0 z1 + y1 z0 + y2 (2 z2),
+    //   L2 = y0 z2 + y1 z1 + y2 z0,
+    // nine 32x32->64 products (2 z1 < 2^31, 2 z2 <= 2^30).
+    static constexpr u32 M30 = (1u << 30) - 1u;
+    static constexpr u32 M29 = (1u << 29) - 1u;
+
+    struct Pow3 {
+        u32 l[3][3];  // x, x^2, x^3, three limbs each
+    };
+
+    // Limbs of (L0 + L1 2^30 + L2 2^60) mod p for L0 < 2^64 - 2^34,
+    // L1, L2 < 2^64 - 2^35 (every caller's sums are below 12 2^60 + 2^30):
+    //   r0 = L0 mod 2^30, L1' = L1 + (L0 >> 30), r1 = L1' mod 2^30,
+    //   L2' = L2 + (L1' >> 30) < 2^64;  L2' 2^60 = (L2' mod 2^29) 2^60 + (L2' >> 29) (mod p)
+    //   s0 = r0 + (L2' >> 29) < 2^30 + 2^35; carries: s1 = r1 + (s0 >> 30) < 2^30 + 33,
+    //   r2 = (L2' mod 2^29) + (s1 >> 30) <= 2^29.
+    __device__ static __forceinline__ void norm3(u64 L0, u64 L1, u64 L2, u32 (&r)[3]) {
+        L1 += L0 >> 30;
+        L2 += L1 >> 30;
+        const u64 s0 = (u64)((u32)L0 & M30) + (L2 >> 29);
+        const u32 s1 = ((u32)L1 & M30) + (u32)(s0 >> 30);
+        r[0] = (u32)s0 & M30;
+        r[1] = s1 & M30;
+        r[2] = ((u32)L2 & M29) + (s1 >> 30);
+    }
+
+    // y * z (mod p), lazy, for lazy y, z (bounds above: L0 < 3 2^60).
+    __device__ static __forceinline__ void mul3(const u32 (&y)[3], const u32 (&z)[3], u32 (&r)[3]) {
+        const u32 z1d = z[1] << 1, z2d = z[2] << 1;
+        u64 L0 = madw(y[0], z[0], 0ull);
+        L0 = madw(y[1], z2d, L0);
+        L0 = madw(y[2], z1d, L0);
+        u64 L1 = madw(y[0], z[1], 0ull);
+        L1 = madw(y[1], z[0], L1);
+        L1 = madw(y[2], z2d, L1);
+        u64 L2 = madw(y[0], z[2], 0ull);
+        L2 = madw(y[1], z[1], L2);
+        L2 = madw(y[2], z[0], L2);
+        norm3(L0, L1, L2, r);
+    }
+
+    // x = (key & p) + (key >> 89) < 2^89 + 2^39 (limb 2 <= 2^29), then x^2, x^3.
+    __device__ static __forceinline__ void powers3(const u128x& key, Pow3& xp) {
+        const u128 v = load(key);
+        const u128 x = (v & Pv()) + (v >> 89);
+        xp.l[0][0] = (u32)x & M30;
+        xp.l[0][1] = (u32)(x >> 30) & M30;
+        xp.l[0][2] = (u32)(x >> 60);
+        mul3(xp.l[0], xp.l[0], xp.l[1]);
+        mul3(xp.l[1], xp.l[0], xp.l[2]);
+    }
+
+    // Bucket and sign bit of y = a0 + a1 x + a2 x^2 + a3 x^3 (mod p).
+    // c: 18 limbs precomputed on the host from canonical coefficients:
+    //   c[0..2] the limbs of a0; for i = 1..3, c[5i-2 .. 5i+2] =
+    //   (a_i0, a_i1, a_i2, 2 a_i1, 2 a_i2) (a_i0, a_i1 < 2^30, a_i2 < 2^29).
+    // Over the three terms the columns are below 3 (4 2^60) + 2^30 (L0),
+    // 9 2^60 + 2^30 (L1, L2).  With y = s0 + r1 2^30 + r2 2^60 after norm3's
+    // first pass (s0 < 2^36 unreduced), the carries of y are u1 = r1 + (s0 >> 30)
+    // and u2 = r2 + (u1 >> 30) <= 2^29, y < 2^89 + 2^36 < 2p, and
+    //   y >= p  <=>  y + 1 >= 2^89  <=>  u2 + [s0, u1 both end in 30 one bits] >= 2^29.
+    // Then the residue y - p = y + 1 - 2^89 < 2^37 has bit 88 clear and the
+    // low 30 bits of s0 + 1; otherwise bit 88 of y is bit 28 of u2.
+    __device__ static __forceinline__ void row_bs(const Pow3& xp, const u32 (&c)[18], u32 mask,
+                                                  u32& bucket, u32& sign) {
+        u64 L0 = c[0], L1 = c[1], L2 = c[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const u32 c0 = c[3 + 5 * i], c1 = c[4 + 5 * i], c2 = c[5 + 5 * i];
+            const u32 d1 = c[6 + 5 * i], d2 = c[7 + 5 * i];
+            const u32 x0 = xp.l[i][0], x1 = xp.l[i][1], x2 = xp.l[i][2];
+            L0 = madw(x0, c0, L0);
+            L0 = madw(x1, d2, L0);
+            L0 = madw(x2, d1, L0);
+            L1 = madw(x0, c1, L1);
+            L1 = madw(x1, c0, L1);
+            L1 = madw(x2, d2, L1);
+            L2 = madw(x0, c2, L2);
+            L2 = madw(x1, c1, L2);
+            L2 = madw(x2, c0, L2);
+        }
+        L1 += L0 >> 30;
+        L2 += L1 >> 30;
+        const u64 s0 = (u64)((u32)L0 & M30) + (L2 >> 29);
+        const u32 u1 = ((u32)L1 & M30) + (u32)(s0 >> 30);
+        const u32 u2 = ((u32)L2 & M29) + (u1 >> 30);
+        const u32 ones = (((u32)s0 & u1 & M30) == M30) ? 1u : 0u;
+        const u32 over = (u2 + ones) >> 29;
+        bucket = ((u32)s0 + over) & mask;
+        sign = over ? 0u : ((u2 >> 28) & 1u);
+    }
+
     // Algorithm Mersenne-arb-r (Sec. 3.3): h' = h + 1, bucket floor(r j / 2^88)
     // for its low 88 bits j (r j < 2^120), a = its top bit.
     __device__ static __forceinline__ void arb_split(u128 h, u32 r, u32& bucket, u32& a) {
@@ -368,6 +500,64 @@ struct P64 {
 
     __device__ static __forceinline__ u32 bucket(u64 h, u32 mask) { return (u32)h & mask; }
     __device__ static __forceinline__ u32 sign_bit(u64 h) { return (u32)(h >> 63); }
+
+    // ---- power sum (the update kernels' row hash for k = 4) ----
+    //
+    // x, x^2, x^3 (canonical) as limbs of 29, 29 and 6 bits:
+    //   x^i = l0 + l1 2^29 + l2 2^58.
+    static constexpr u32 M29 = (1u << 29) - 1u;
+    struct Pow3 {
+        u32 l[3][3];
+    };
+
+    __device__ static __forceinline__ void split29(u64 z, u32 (&l)[3]) {
+        l[0] = (u32)z & M29;
+        l[1] = (u32)(z >> 29) & M29;
+        l[2] = (u32)(z >> 58);
+    }
+
+    __device__ static __forceinline__ void powers3(u64 key, Pow3& xp) {
+        const u64 x = reduce_key(key);
+        const u64 x2 = mod_p((u128)x * x);
+        split29(x, xp.l[0]);
+        split29(x2, xp.l[1]);
+        split29(mod_p((u128)x2 * x), xp.l[2]);
+    }
+
+    // Bucket and sign bit of y = a0 + a1 x + a2 x^2 + a3 x^3 (mod p).
+    // c: 18 words precomputed on the host, for i = 1..3 and v = 0..2 the low and
+    // high 32-bit halves of b_iv = a_i 2^(29 v) mod p, at c[6(i-1) + 2v + {0,1}];
+    // then a_i x^i = sum_v l_iv b_iv (mod p).  Columns of weight 1 and 2^32:
+    //   L0 = a0.lo + sum l_iv b_iv.lo,  L1 = a0.hi + sum l_iv b_iv.hi,
+    // each below 2^32 + 6 2^61 + 3 2^38 < 2^64 (l_i0, l_i1 < 2^29, l_i2 < 2^6).
+    // V = L0 + L1 2^32 = vh 2^64 + vl with vh < 2^32 (L1 < 0.76 2^64).
+    // V < 2^96 < (2^64/59)^2, so two steps of Algorithm division-generalized
+    // give z = floor(V / p) (Thm simple-div, Sec. 4), and Algorithm
+    // mod-generalized the canonical y = (V + 59 z) mod 2^64:
+    //   v' = V + 59;  z = v' >> 64;  z = (59 z + v') >> 64
+    //     = v'.hi + carry(v'.lo + 59 v'.hi).
+    __device__ static __forceinline__ void row_bs(const Pow3& xp, u64 a0, const u32 (&c)[18],
+                                                  u32 mask, u32& bucket, u32& sign) {
+        u64 L0 = a0 & 0xFFFFFFFFull, L1 = a0 >> 32;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                L0 = madw(xp.l[i][v], c[6 * i + 2 * v], L0);
+                L1 = madw(xp.l[i][v], c[6 * i + 2 * v + 1], L1);
+            }
+        }
+        const u64 t = (L0 >> 32) + (L1 & 0xFFFFFFFFull);  // < 2^33
+        const u64 vl = (L0 & 0xFFFFFFFFull) | (t << 32);
+        const u32 vh = (u32)(L1 >> 32) + (u32)(t >> 32);
+        const u64 vpl = vl + C;
+        const u32 vph = vh + (vpl < vl ? 1u : 0u);
+        const u64 q = (u64)vph * C;
+        const u32 z = vph + ((vpl + q) < vpl ? 1u : 0u);
+        const u64 y = vl + (u64)z * C;
+        bucket = (u32)y & mask;
+        sign = (u32)(y >> 63);
+    }
 };
 
 }  // namespace msf
