@@ -12,9 +12,11 @@ namespace msk {
 //
 // Output of Algorithm count-sketch per row, X_r = sum_i C[r][i]^2, as an exact
 // 128-bit sum (two 64-bit limbs with carry), then the median of the t rows.
-// Grid: t * splits blocks; block (row, split) sums one slice of one row and
-// writes a partial; the last block to finish (atomic ticket) adds the
-// partials, takes the median, writes the result and re-arms the ticket.
+// Small sketches (t * m <= F2_ONE_BLOCK_CELLS): one block, its warps split
+// evenly over the rows.  Larger ones: t * splits blocks, block (row, split)
+// sums one slice of one row and writes a partial; the last block to finish
+// (atomic ticket) adds the partials, takes the median, writes the result and
+// re-arms the ticket.
 
 struct U128 {
     u64 lo, hi;
@@ -30,26 +32,82 @@ __device__ __forceinline__ bool less128(const U128& a, const U128& b) {
     return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }
 
-__global__ void __launch_bounds__(1024) k_cs_f2(const F2Args a) {
-    __shared__ U128 warp_sums[32];
-    __shared__ bool is_last;
-    const int row = blockIdx.x / a.splits;
-    const int split = blockIdx.x % a.splits;
-    const u32 slice = a.m / (u32)a.splits;
-    const long long* c = a.counters + (u64)row * a.m + (u64)split * slice;
+constexpr u32 F2_ONE_BLOCK_CELLS = 1u << 15;
 
-    U128 acc = {0ull, 0ull};
-    for (u32 i = threadIdx.x; i < slice; i += blockDim.x) {
+// acc += sum of C[i]^2 over the counters this lane visits
+__device__ __forceinline__ void sumsq(U128& acc, const long long* c, u32 begin, u32 end, u32 step) {
+    for (u32 i = begin; i < end; i += step) {
         const long long v = __ldcg(c + i);
         const u64 mag = v < 0 ? 0ull - (u64)v : (u64)v;
         add128(acc, mag * mag, __umul64hi(mag, mag));
     }
+}
+
+__device__ __forceinline__ void warp_sum128(U128& acc) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const u64 lo = __shfl_down_sync(0xffffffffu, acc.lo, off);
         const u64 hi = __shfl_down_sync(0xffffffffu, acc.hi, off);
         add128(acc, lo, hi);
     }
+}
+
+// The median of the t row values in shared memory (t odd): thread r < t finds
+// the rank of row r, ties broken by index, and the one of rank t/2 writes it.
+// Also writes the row values when asked.  Called by every thread of a block.
+__device__ __forceinline__ void median_rows(const U128* rows, int t, ms_u128* out, ms_u128* rows_out) {
+    const int r = threadIdx.x;
+    if (r < t) {
+        const U128 x = rows[r];
+        int rank = 0;
+        for (int j = 0; j < t; ++j) {
+            const U128 y = rows[j];
+            rank += (less128(y, x) || (j < r && y.lo == x.lo && y.hi == x.hi)) ? 1 : 0;
+        }
+        if (rank == t / 2) {
+            out->lo = x.lo;
+            out->hi = x.hi;
+        }
+        if (rows_out) {
+            rows_out[r].lo = x.lo;
+            rows_out[r].hi = x.hi;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_cs_f2_one(const F2Args a) {
+    __shared__ U128 warp_sums[32];
+    __shared__ U128 rows[MAX_T];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpr = (int)(blockDim.x >> 5) / a.t;  // warps per row (>= 2: t <= 15)
+    const int row = warp / wpr, sub = warp % wpr;
+    U128 acc = {0ull, 0ull};
+    if (row < a.t)
+        sumsq(acc, a.counters + (u64)row * a.m, (u32)(sub * 32 + lane), a.m, (u32)wpr * 32u);
+    warp_sum128(acc);
+    if (lane == 0) warp_sums[warp] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < a.t) {
+        U128 s = {0ull, 0ull};
+        for (int q = 0; q < wpr; ++q) add128(s, warp_sums[threadIdx.x * wpr + q].lo,
+                                             warp_sums[threadIdx.x * wpr + q].hi);
+        rows[threadIdx.x] = s;
+    }
+    __syncthreads();
+    median_rows(rows, a.t, a.out, a.rows);
+}
+
+__global__ void __launch_bounds__(1024) k_cs_f2(const F2Args a) {
+    __shared__ U128 warp_sums[32];
+    __shared__ U128 rows[MAX_T];
+    __shared__ bool is_last;
+    const int row = blockIdx.x / a.splits;
+    const int split = blockIdx.x % a.splits;
+    const u32 slice = a.m / (u32)a.splits;
+
+    U128 acc = {0ull, 0ull};
+    sumsq(acc, a.counters + (u64)row * a.m + (u64)split * slice, threadIdx.x, slice, blockDim.x);
+    warp_sum128(acc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) warp_sums[warp] = acc;
     __syncthreads();
@@ -64,38 +122,27 @@ __global__ void __launch_bounds__(1024) k_cs_f2(const F2Args a) {
         is_last = (prev == gridDim.x - 1);
     }
     __syncthreads();
-    if (!is_last || threadIdx.x != 0) return;
+    if (!is_last) return;
 
+    // the last block: thread r adds row r's partials (loads from L2, where the
+    // other blocks' fenced writes are)
     __threadfence();
-    U128 rows[MAX_T];
-    for (int r = 0; r < a.t; ++r) {
+    if ((int)threadIdx.x < a.t) {
         U128 s = {0ull, 0ull};
-        for (int q = 0; q < a.splits; ++q) {
-            const volatile u64* pw = (const volatile u64*)(a.partial + r * a.splits + q);
-            add128(s, pw[0], pw[1]);
-        }
-        rows[r] = s;
-        if (a.rows) {
-            a.rows[r].lo = s.lo;
-            a.rows[r].hi = s.hi;
-        }
+        const ms_u128* pr = a.partial + threadIdx.x * a.splits;
+        for (int q = 0; q < a.splits; ++q) add128(s, __ldcg(&pr[q].lo), __ldcg(&pr[q].hi));
+        rows[threadIdx.x] = s;
     }
-    for (int i = 1; i < a.t; ++i) {  // insertion sort, t <= 15
-        U128 x = rows[i];
-        int j = i - 1;
-        while (j >= 0 && less128(x, rows[j])) {
-            rows[j + 1] = rows[j];
-            --j;
-        }
-        rows[j + 1] = x;
-    }
-    a.out->lo = rows[a.t / 2].lo;
-    a.out->hi = rows[a.t / 2].hi;
-    *a.ticket = 0u;  // re-arm for the next launch on this scratch
+    __syncthreads();
+    median_rows(rows, a.t, a.out, a.rows);
+    if (threadIdx.x == 0) *a.ticket = 0u;  // re-arm for the next launch on this scratch
 }
 
 cudaError_t launch_cs_f2(const F2Args& a, int threads, cudaStream_t stream) {
-    k_cs_f2<<<a.t * a.splits, threads, 0, stream>>>(a);
+    if ((u64)a.t * a.m <= F2_ONE_BLOCK_CELLS)
+        k_cs_f2_one<<<1, 1024, 0, stream>>>(a);
+    else
+        k_cs_f2<<<a.t * a.splits, threads, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
