@@ -318,9 +318,10 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  *            into the counters.
  *  Default: 0 when the t*m int32 tile fits 112 KiB, else 2.
  *  strategy: 0 = Horner per row (Algorithm Mersenne), 1 = powers of x once per
- *            key, then sum a_i x^i per row (only for p = 2^61-1 with k = 4;
- *            other sketches use Horner).  Both give identical hash values.
- *  threads (multiple of 32, <= 512; default 512 for place 2 and 3), blocks
+ *            key, then sum a_i x^i per row (k = 4 with t = 5 or 7, every prime;
+ *            for the other primes only with a power-of-two m; other sketches
+ *            use Horner).  Both give identical hash values.
+ *  threads (multiple of 32, <= 512; default 512, 256 for place 1), blocks
  *  (total), blocks_per_sm (cap), cluster (power of two <= 16, place 1 only),
  *  replicas (power of two <= 32, place 2 only; capped at the replicas the
  *  sketch owns; default 16),

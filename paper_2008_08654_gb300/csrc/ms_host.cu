@@ -540,9 +540,11 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
             cfg.cluster = cl;
     }
     cfg.place = place;
-    // global placement: 512-thread blocks (measured on the 2^28-key Zipf sketch:
-    // 3% faster than 256 with 16 replicas)
-    if (ov.threads <= 0 && place == msk::PLACE_GLOBAL) cfg.threads = 512;
+    // 512-thread blocks for the shared-memory tile and global placements (the
+    // global one measured 3% faster than 256 on the 2^28-key Zipf sketch; with
+    // t = 5, m = 4096 tiles, where shared memory admits two blocks per SM,
+    // 512 threads were 6-8% faster than 256 for every prime)
+    if (ov.threads <= 0 && place != msk::PLACE_DSMEM) cfg.threads = 512;
     cfg.replicas = 0;
     // With the de-duplication table (unit weights, one-word keys) the hottest
     // keys reach the counters once per block, so fewer replicas suffice (8 vs
