@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(1024) k_cs_update_batched(const BatchArgs a) {
                     if (wt[q] == 0) continue;  // ragged end of the chunk
                     msf::P61::Pow3 xp;
                     msf::P61::powers3(key[q], xp);
-                    for (int r = r0; r < r1; ++r) {
+                    auto row = [&](int r) {
                         const PsCoef cb = sps[(r - r0) * NF];
                         u32 ylo, yhi, bucket, sb;
                         msf::P61::row_kara(xp, cb.lo, cb.hi, cb.nd, cb.a0, a.c2p31, a.c4, ylo, yhi);
@@ -133,6 +133,14 @@ __global__ void __launch_bounds__(1024) k_cs_update_batched(const BatchArgs a) {
                             msf::P61::bucket_sign_hl(ylo, yhi, mask, unused, sb);
                         }
                         batched_add(tile, job.counters, r, r0, log2m, bucket, sb, wt[q], big[q]);
+                    };
+                    if (r1 - r0 == 5) {
+                        // five rows (every item of a t = 5 sketch): unrolled, so
+                        // the rows' multiply chains interleave
+#pragma unroll
+                        for (int rr = 0; rr < 5; ++rr) row(r0 + rr);
+                    } else {
+                        for (int r = r0; r < r1; ++r) row(r);
                     }
                 }
             } else {

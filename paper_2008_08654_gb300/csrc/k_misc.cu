@@ -34,12 +34,21 @@ __device__ __forceinline__ bool less128(const U128& a, const U128& b) {
 
 constexpr u32 F2_ONE_BLOCK_CELLS = 1u << 15;
 
-// acc += sum of C[i]^2 over the counters this lane visits
+// acc += sum of C[i]^2 over the counters this lane visits (i = begin, begin +
+// step, ... < end), eight loads in flight before any of them is used
 __device__ __forceinline__ void sumsq(U128& acc, const long long* c, u32 begin, u32 end, u32 step) {
-    for (u32 i = begin; i < end; i += step) {
-        const long long v = __ldcg(c + i);
-        const u64 mag = v < 0 ? 0ull - (u64)v : (u64)v;
-        add128(acc, mag * mag, __umul64hi(mag, mag));
+    for (u32 i = begin; i < end; i += 8u * step) {
+        long long v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const u32 j = i + (u32)u * step;
+            v[u] = j < end ? __ldcg(c + j) : 0ll;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const u64 mag = v[u] < 0 ? 0ull - (u64)v[u] : (u64)v[u];
+            add128(acc, mag * mag, __umul64hi(mag, mag));
+        }
     }
 }
 
