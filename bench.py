@@ -758,7 +758,9 @@ def run_serving(args):
               for x in datagen.u64_below(args.seed, 2, S, stream=datagen.STREAM_WIDTHS)]
     srv = ms.Server(widths, t=5, seed_base=args.seed, staging_bytes=40 << 30, max_inflight=4096,
                     max_batch_keys=1 << 25, max_batch_requests=4096, timeout_s=120.0)
-    pool = torch.from_numpy(datagen.zipf(args.seed, 1.1, 1 << 32, 1 << 22).view(np.int64))
+    # 2^26 keys (512 MiB, larger than the L2): page-locked, so the update kernel
+    # reads each request's keys in place over the host link
+    pool = torch.from_numpy(datagen.zipf(args.seed, 1.1, 1 << 32, 1 << 26).view(np.int64))
     pool = pool.pin_memory()
     count = max(200, args.keys or 4000)
     qf, lo, hi = 0.1, 256, 1 << 20
@@ -778,7 +780,8 @@ def run_serving(args):
                  "keys/s", args,
                  {"workload": "%d device-resident sketches, m in {1024, 4096}; %d requests per "
                               "run, 10%% F2 queries, updates of log-uniform 256..2^20 Zipf(1.1) "
-                              "keys from a pinned host pool; 40 GB staging" % (S, count)},
+                              "keys from a page-locked host pool of 2^26 keys (512 MiB), read in place by "
+                              "the update kernel; 40 GB staging" % (S, count)},
                  saturated=peak, offered_load=levels)
 
 

@@ -55,11 +55,13 @@ ms_status ms_server_create(ms_server** out, const ms_server_config* cfg);
 /*
  * ms_server_submit_update -- queue n keys (and int32 weights, or NULL for unit
  * weights) for sketch `sketch_id`.  The host buffers are read when the request
- * is admitted into a batch and must stay valid until it is done; pinned
- * (page-locked) buffers let the copy overlap compute.  Blocks while no slot is
- * free (at most timeout_s, then MS_ERR_TIMEOUT); with try_only != 0 returns
- * MS_ERR_BUSY instead.  An update larger than the whole staging ring is
- * rejected with MS_ERR_OUT_OF_RANGE.  *ticket identifies the request.
+ * is admitted into a batch and must stay valid until it is done.  Page-locked
+ * buffers (cudaMallocHost, cudaHostRegister, a pinned torch tensor) are read in
+ * place by the update kernel and take no staging space; pageable ones are
+ * copied into the staging ring.  Blocks while no slot is free (at most
+ * timeout_s, then MS_ERR_TIMEOUT); with try_only != 0 returns MS_ERR_BUSY
+ * instead.  A pageable update larger than the whole staging ring is rejected
+ * with MS_ERR_OUT_OF_RANGE.  *ticket identifies the request.
  */
 ms_status ms_server_submit_update(ms_server* s, int sketch_id, const void* keys_host,
                                   const int32_t* weights_host, uint64_t n, int try_only,

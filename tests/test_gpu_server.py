@@ -124,3 +124,50 @@ def test_load_generator_runs():
     assert r["updates"] + r["queries"] == 300 and r["keys"] > 0
     assert 0 < r["update_p50_ms"] <= r["update_p99_ms"]
     srv.close()
+
+
+def test_server_page_locked_payloads_read_in_place():
+    """Updates from page-locked buffers (read in place by the kernel, no staging
+    copy) and from pageable ones (copied), mixed in batches, misaligned slices
+    among them; a page-locked update larger than the whole staging ring is
+    accepted, a pageable one is not."""
+    import torch
+    import paper_2008_08654_gb300 as ms
+    widths, t, seed_base = [64, 1024, 4096], 5, 91
+    reqs = _requests(len(widths), 60, 9)
+    pinned = []
+    for i, (kind, s, keys, w) in enumerate(reqs):
+        if kind == "u" and i % 2 == 0:
+            kp = torch.from_numpy(keys.view(np.int64)).pin_memory()
+            wp = None if w is None else torch.from_numpy(w).pin_memory()
+            if i % 4 == 0 and len(keys) > 1:  # an 8-byte offset: scalar loads
+                buf = torch.empty(len(keys) + 1, dtype=torch.int64).pin_memory()
+                buf[1:] = kp
+                kp = buf[1:]
+            pinned.append((kp, wp))
+            reqs[i] = (kind, s, keys, w, kp, wp)
+    big = datagen.zipf(3, 1.1, 1 << 16, 20000)
+    reqs.append(("u", 2, big, None, torch.from_numpy(big.view(np.int64)).pin_memory(), None))
+    reqs.append(("q", 2, None, None))
+    want, want_c = _expected([r[:4] for r in reqs], widths, t, seed_base)
+    srv = ms.Server(widths, t=t, seed_base=seed_base, staging_bytes=64 << 10)
+    with pytest.raises(ms.MSError):
+        srv.submit_update(2, big)  # pageable and larger than the ring
+    tickets = []
+    for r in reqs:
+        if r[0] == "u":
+            keys, w = (r[4], r[5]) if len(r) == 6 else (r[2], r[3])
+            tickets.append(("u", srv.submit_update(r[1], keys, w)))
+        else:
+            tickets.append(("q", srv.submit_query(r[1])))
+    srv.drain()
+    ans = []
+    for kind, tk in tickets:
+        res = srv.poll(tk)
+        assert res["done"] and res["status"] == 0
+        if kind == "q":
+            ans.append(res["f2"])
+    assert ans == want
+    for i, c in enumerate(want_c):
+        assert np.array_equal(srv.counters(i), c)
+    srv.close()
