@@ -154,11 +154,13 @@ __device__ __forceinline__ void split_row(const typename FieldOps<F>::val_t& h,
 // constant offset, so the multiply instructions read them straight from the
 // constant bank.  For p = 2^61-1 the 31-bit splits used by the power-sum
 // evaluation are precomputed on the host.
-// For 2^89-1 and 2^64-59 the power sum also takes 18 precomputed limbs per
-// function (k = 4), built by fill_param_coef.
+// For 2^89-1 and 2^64-59 the power sum also takes 21 and 18 precomputed words
+// per function (k = 4), built by fill_param_coef.
 template <class F>
 struct PsLimbs {
-    static constexpr int N = (std::is_same<F, msf::P89>::value || std::is_same<F, msf::P64>::value) ? 18 : 0;
+    static constexpr int N = std::is_same<F, msf::P89>::value   ? 21
+                             : std::is_same<F, msf::P64>::value ? 18
+                                                                : 0;
 };
 
 template <class F, int NFUN, int K>
@@ -436,9 +438,10 @@ __device__ __forceinline__ void ps_row_bs(const typename F::Pow3& xp, const PC& 
             F::row_bs(xp, (u32)pc.w[f * 4], (u32)pc.w[f * 4 + 1], (u32)pc.w[f * 4 + 2],
                       (u32)pc.w[f * 4 + 3], mask, b, s);
         } else {
-            u32 c[18];
+            constexpr int N = PsLimbs<F>::N;
+            u32 c[N];
 #pragma unroll
-            for (int i = 0; i < 18; ++i) c[i] = pc.ps[f * 18 + i];
+            for (int i = 0; i < N; ++i) c[i] = pc.ps[f * N + i];
             if constexpr (std::is_same<F, msf::P64>::value)
                 F::row_bs(xp, pc.w[f * 4], c, mask, b, s);
             else

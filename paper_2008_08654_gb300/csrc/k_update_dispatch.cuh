@@ -32,10 +32,11 @@ static void fill_param_coef(ParamCoef<F, NFUN, K>& pc, const u64* words) {
     }
     if constexpr (K == 4 && PsLimbs<F>::N > 0) {
         for (int f = 0; f < NFUN; ++f) {
-            u32* c = pc.ps + f * 18;
+            u32* c = pc.ps + f * PsLimbs<F>::N;
             const u64* a = words + (size_t)f * K * W;
             if constexpr (std::is_same<F, msf::P89>::value) {
-                // a0's 30-bit limbs, then (l0, l1, l2, 2 l1, 2 l2) of a1, a2, a3
+                // a0's 30-bit limbs, then (l0, l1, l2, l0 - l1, l0 - l2, l1 - l2)
+                // of a1, a2, a3 (the differences as two's-complement words)
                 for (int i = 0; i < 4; ++i) {
                     const unsigned __int128 v = ((unsigned __int128)a[2 * i + 1] << 64) | a[2 * i];
                     const u32 l0 = (u32)(v & 0x3FFFFFFFu), l1 = (u32)((v >> 30) & 0x3FFFFFFFu);
@@ -43,8 +44,11 @@ static void fill_param_coef(ParamCoef<F, NFUN, K>& pc, const u64* words) {
                     if (i == 0) {
                         c[0] = l0; c[1] = l1; c[2] = l2;
                     } else {
-                        u32* d = c + 3 + 5 * (i - 1);
-                        d[0] = l0; d[1] = l1; d[2] = l2; d[3] = 2 * l1; d[4] = 2 * l2;
+                        u32* d = c + 3 + 6 * (i - 1);
+                        d[0] = l0; d[1] = l1; d[2] = l2;
+                        d[3] = (u32)((int)l0 - (int)l1);
+                        d[4] = (u32)((int)l0 - (int)l2);
+                        d[5] = (u32)((int)l1 - (int)l2);
                     }
                 }
             } else {

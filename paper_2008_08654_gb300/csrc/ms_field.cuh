@@ -37,6 +37,13 @@ __device__ __forceinline__ u64 madw(u32 a, u32 b, u64 c) {
     return d;
 }
 
+// The signed form: a * b + c modulo 2^64, a and b signed 32-bit.
+__device__ __forceinline__ u64 madws(int a, int b, u64 c) {
+    u64 d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
 // ---------------------------------------------------------------- p = 2^61-1
 //
 // Elements are split into a 31-bit low part and a high part,
@@ -360,6 +367,7 @@ struct P89 {
 
     struct Pow3 {
         u32 l[3][3];  // x, x^2, x^3, three limbs each
+        int d[3][3];  // per power: l1 - l0, l2 - l0, l2 - l1
     };
 
     // Limbs of (L0 + L1 2^30 + L2 2^60) mod p for L0 < 2^64 - 2^34,
@@ -393,6 +401,36 @@ struct P89 {
         norm3(L0, L1, L2, r);
     }
 
+    // One Horner step (Algorithm Mersenne) on limbs: r = y x + a (mod p), lazy,
+    // for lazy y, x and a canonical a: a's limbs join the columns before the
+    // carry pass (L0 < 3 2^60 + 2^30, within norm3's bounds).
+    __device__ static __forceinline__ void mul_add3(const u32 (&y)[3], const u32 (&x)[3],
+                                                    const u32 (&a)[3], u32 (&r)[3]) {
+        const u32 x1d = x[1] << 1, x2d = x[2] << 1;
+        u64 L0 = madw(y[0], x[0], (u64)a[0]);
+        L0 = madw(y[1], x2d, L0);
+        L0 = madw(y[2], x1d, L0);
+        u64 L1 = madw(y[0], x[1], (u64)a[1]);
+        L1 = madw(y[1], x[0], L1);
+        L1 = madw(y[2], x2d, L1);
+        u64 L2 = madw(y[0], x[2], (u64)a[2]);
+        L2 = madw(y[1], x[1], L2);
+        L2 = madw(y[2], x[0], L2);
+        norm3(L0, L1, L2, r);
+    }
+
+    // The three limbs of a value below 2^90.
+    __device__ static __forceinline__ void limbs(u128 v, u32 (&l)[3]) {
+        l[0] = (u32)v & M30;
+        l[1] = (u32)(v >> 30) & M30;
+        l[2] = (u32)(v >> 60);
+    }
+
+    // The canonical residue of lazy limbs (value < 2^89 + 2^60 < 2p).
+    __device__ static __forceinline__ u128 canon3(const u32 (&l)[3]) {
+        return canon((u128)l[0] | ((u128)l[1] << 30) | ((u128)l[2] << 60));
+    }
+
     // x = (key & p) + (key >> 89) < 2^89 + 2^39 (limb 2 <= 2^29), then x^2, x^3.
     __device__ static __forceinline__ void powers3(const u128x& key, Pow3& xp) {
         const u128 v = load(key);
@@ -402,37 +440,55 @@ struct P89 {
         xp.l[0][2] = (u32)(x >> 60);
         mul3(xp.l[0], xp.l[0], xp.l[1]);
         mul3(xp.l[1], xp.l[0], xp.l[2]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            xp.d[i][0] = (int)xp.l[i][1] - (int)xp.l[i][0];
+            xp.d[i][1] = (int)xp.l[i][2] - (int)xp.l[i][0];
+            xp.d[i][2] = (int)xp.l[i][2] - (int)xp.l[i][1];
+        }
     }
 
     // Bucket and sign bit of y = a0 + a1 x + a2 x^2 + a3 x^3 (mod p).
-    // c: 18 limbs precomputed on the host from canonical coefficients:
-    //   c[0..2] the limbs of a0; for i = 1..3, c[5i-2 .. 5i+2] =
-    //   (a_i0, a_i1, a_i2, 2 a_i1, 2 a_i2) (a_i0, a_i1 < 2^30, a_i2 < 2^29).
-    // Over the three terms the columns are below 3 (4 2^60) + 2^30 (L0),
-    // 9 2^60 + 2^30 (L1, L2).  With y = s0 + r1 2^30 + r2 2^60 after norm3's
-    // first pass (s0 < 2^36 unreduced), the carries of y are u1 = r1 + (s0 >> 30)
-    // and u2 = r2 + (u1 >> 30) <= 2^29, y < 2^89 + 2^36 < 2p, and
-    //   y >= p  <=>  y + 1 >= 2^89  <=>  u2 + [s0, u1 both end in 30 one bits] >= 2^29.
-    // Then the residue y - p = y + 1 - 2^89 < 2^37 has bit 88 clear and the
-    // low 30 bits of s0 + 1; otherwise bit 88 of y is bit 28 of u2.
-    __device__ static __forceinline__ void row_bs(const Pow3& xp, const u32 (&c)[18], u32 mask,
+    // c: 21 words precomputed on the host from canonical coefficients: c[0..2]
+    // the limbs of a0; for i = 1..3, c[6i-3 .. 6i+2] = (l0, l1, l2, l0 - l1,
+    // l0 - l2, l1 - l2) of a_i (l0, l1 < 2^30, l2 < 2^29; differences signed).
+    // Each product a_i x^i is taken by Karatsuba, six 32x32->64 products
+    // instead of nine: with P_jj = l_j x_j and D_jk = (l_j - l_k)(x_k - x_j),
+    //   l0 x1 + l1 x0 = P00 + P11 + D01,  l0 x2 + l2 x0 = P00 + P22 + D02,
+    //   l1 x2 + l2 x1 = P11 + P22 + D12,
+    // and the wrapped columns of mul3 become
+    //   L0 = P00 + 2 (P11 + P22 + D12),  L1 = P00 + P11 + 2 P22 + D01,
+    //   L2 = P00 + P11 + P22 + D02.
+    // Summed over the three terms (S_jj, T_jk) with U = S00 + S11 + S22:
+    //   L0 = 2 (U + T12) - S00 + a0.l0,  L1 = U + S22 + T01 + a0.l1,
+    //   L2 = U + T02 + a0.l2,
+    // computed modulo 2^64 (the T's are signed); each column's true value is
+    // below 12 2^60 + 2^30 (as in the nine-product form), so the results are
+    // exact.  Then the columns are normalised as below.
+    __device__ static __forceinline__ void row_bs(const Pow3& xp, const u32 (&c)[21], u32 mask,
                                                   u32& bucket, u32& sign) {
-        u64 L0 = c[0], L1 = c[1], L2 = c[2];
+        u64 S00 = 0, S11 = 0, S22 = 0;
+        u64 T01 = c[1], T02 = c[2], T12 = 0;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const u32 c0 = c[3 + 5 * i], c1 = c[4 + 5 * i], c2 = c[5 + 5 * i];
-            const u32 d1 = c[6 + 5 * i], d2 = c[7 + 5 * i];
-            const u32 x0 = xp.l[i][0], x1 = xp.l[i][1], x2 = xp.l[i][2];
-            L0 = madw(x0, c0, L0);
-            L0 = madw(x1, d2, L0);
-            L0 = madw(x2, d1, L0);
-            L1 = madw(x0, c1, L1);
-            L1 = madw(x1, c0, L1);
-            L1 = madw(x2, d2, L1);
-            L2 = madw(x0, c2, L2);
-            L2 = madw(x1, c1, L2);
-            L2 = madw(x2, c0, L2);
+            const u32* a = c + 3 + 6 * i;
+            S00 = madw(a[0], xp.l[i][0], S00);
+            S11 = madw(a[1], xp.l[i][1], S11);
+            S22 = madw(a[2], xp.l[i][2], S22);
+            T01 = madws((int)a[3], xp.d[i][0], T01);
+            T02 = madws((int)a[4], xp.d[i][1], T02);
+            T12 = madws((int)a[5], xp.d[i][2], T12);
         }
+        const u64 U = S00 + S11 + S22;
+        u64 L2 = U + T02;
+        u64 L1 = U + S22 + T01;
+        u64 L0 = 2ull * (U + T12) - S00 + c[0];
+        // With y = s0 + r1 2^30 + r2 2^60 after norm3's first pass (s0 < 2^36
+        // unreduced), the carries of y are u1 = r1 + (s0 >> 30) and
+        // u2 = r2 + (u1 >> 30) <= 2^29, y < 2^89 + 2^36 < 2p, and
+        //   y >= p  <=>  y + 1 >= 2^89  <=>  u2 + [s0, u1 both end in 30 one bits] >= 2^29.
+        // Then the residue y - p = y + 1 - 2^89 < 2^37 has bit 88 clear and the
+        // low 30 bits of s0 + 1; otherwise bit 88 of y is bit 28 of u2.
         L1 += L0 >> 30;
         L2 += L1 >> 30;
         const u64 s0 = (u64)((u32)L0 & M30) + (L2 >> 29);
