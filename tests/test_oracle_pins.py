@@ -137,6 +137,34 @@ def test_oracle_agrees_with_paper_division(b, c):
             assert 0 <= qq - _paper_division(v, b, c, n - 1) <= 1
 
 
+@pytest.mark.parametrize("b", [31, 61])
+def test_branch_free_division_on_1e7_random_values(b):
+    """Algorithm div-simple (Sec. 1.5) for p = 2^b - 1 and v < 2^(2b), restated
+    branch free on 64-bit words (numpy) -- v' = v + 1, z = ((v' >> b) + v') >> b,
+    y = (v + z) & p -- equals the oracle's / and % on 10^7 random values."""
+    n = 10 ** 7
+    p = np.uint64((1 << b) - 1)
+    v = datagen.u128_bits(1000 + b, 2 * b, n)
+    vl, vh = v[:, 0].copy(), v[:, 1].copy()
+    one = np.uint64(1)
+    sb, s64b = np.uint64(b), np.uint64(64 - b)
+    # v' = v + 1 (with the carry into the high word)
+    pl = vl + one
+    ph = vh + (pl == 0).astype(np.uint64)
+    # v' >> b  (< 2^b + 1 for v < 2^(2b)), then + v'
+    z1 = (pl >> sb) | (ph << s64b) if b < 64 else ph
+    sl = pl + z1
+    sh = ph + (sl < z1).astype(np.uint64)
+    z = (sl >> sb) | (sh << s64b)
+    y = (vl + z) & p
+    q, r = oracle.divmod_(b, 1, v)
+    assert not q[:, 1].any() and not r[:, 1].any()
+    assert np.array_equal(z, q[:, 0])
+    assert np.array_equal(y, r[:, 0])
+    # the whole range was reached: the largest inputs are near 2^(2b)
+    assert int(vh.max()) >> max(0, 2 * b - 64 - 4) > 0 if 2 * b > 64 else int(vl.max()) >> (2 * b - 4) > 0
+
+
 def test_division_step_counts():
     """Step counts implied by the division theorem: c=1 needs 2 steps below 2^(2b)
     (Algorithm div-simple); 2^64-59 needs 3 steps for all of [0, 2^128) and 2
