@@ -51,3 +51,23 @@ def test_large_sketch_full_size():
 def test_large_sketch_two_poly_quarter():
     """Two polynomials per row on the first 2^26 keys of the same stream."""
     _run("large-twopoly", n=1 << 26)
+
+
+@pytest.mark.parametrize("b,c,k", [(61, 1, 4), (31, 1, 4), (89, 1, 4), (89, 1, 8), (64, 59, 4)])
+def test_hash_eval_1e7_keys(b, c, k):
+    """Every hash value of 10^7 keys (edge keys first, the rest uniform over the
+    key type) equals the oracle's, bit for bit."""
+    import torch
+
+    import paper_2008_08654_gb300 as ms
+    from test_gpu_parity import hash_to_np, make_keys, to_dev
+    n = 10 ** 7
+    keys = make_keys(b, c, n, 4000 + b + k)
+    h = ms.Hash(k=k, b=b, c=c, seed=31 * b + k)
+    got = hash_to_np(torch, h.eval(to_dev(torch, keys)), b)
+    want = oracle.hash_eval(b, c, oracle.from_ints(h.coeffs()), keys)
+    if b == 89:
+        assert np.array_equal(got, want)
+    else:
+        assert not want[:, 1].any()
+        assert np.array_equal(got, want[:, 0])
