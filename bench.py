@@ -85,6 +85,8 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=2008)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload: skip the plain-2^28 and batched sub-results")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--keys", type=int, default=0,
@@ -166,6 +168,78 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------------ roofline
+
+def mad_wide_per_entry(t: int, nf: int) -> int:
+    """32x32->64 multiply-adds (mad.wide) one hashed entry costs in the 2^61-1,
+    k = 4 update kernels, counted from the row code (ms_field.cuh, row_sd and
+    powers3): per row 9 products (Karatsuba on signed 31-bit digits) and 2
+    fold steps (2^31 and 4 as wide multiply-adds); per key x^2 (3) and x^3 (4)."""
+    return 11 * t * nf + 7
+
+
+def hbm_peak_gbs() -> tuple:
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), \
+            "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return 6787.9, "fallback: the pool's measured copy bandwidth recorded for this project"
+
+
+def probe_peaks(ms) -> dict:
+    """Integer-multiply peaks of this GPU, measured in this run: 64x64->128
+    products (the roofline's denominator) and 32x32->64 multiply-adds (the
+    instruction the kernels issue: the best of the dependent-chain and the
+    16-chain probes)."""
+    mul_rate, _ = ms.probe_mul128(variant=0, iters=1 << 12)
+    madw_dep, _ = ms.probe_mul128(variant=1, iters=1 << 13)
+    madw_ind, _ = ms.probe_mul128(variant=4, iters=1 << 12)
+    return {"mul128_per_s": mul_rate, "mad_wide_dependent_per_s": madw_dep,
+            "mad_wide_independent_per_s": madw_ind, "mad_wide_per_s": max(madw_dep, madw_ind)}
+
+
+def roofline_8d(n: int, t: int, nf: int, bytes_per_key: int, kern_s: float, peaks: dict,
+                hbm_gbs: float, hbm_src: str) -> dict:
+    """The roofline of the hot-path table's measurement row:
+        roofline_time = max(n * bytes_per_key / HBM, n * t (k-1) / PEAK_mul128)
+    over all n keys of the launch (the method's work, whatever the kernel
+    skips), frac = roofline_time / kernel time."""
+    mul_per_key = t * 3 * nf
+    hbm_s = n * bytes_per_key / (hbm_gbs * 1e9)
+    mul_s = n * mul_per_key / peaks["mul128_per_s"]
+    if mul_s >= hbm_s:
+        r = {"bound": "alu", "achieved": n * mul_per_key / kern_s / 1e9,
+             "peak": peaks["mul128_per_s"] / 1e9, "unit": "Gmul128/s"}
+    else:
+        r = {"bound": "hbm", "achieved": n * bytes_per_key / kern_s / 1e9, "peak": hbm_gbs,
+             "unit": "GB/s"}
+    r["frac"] = max(hbm_s, mul_s) / kern_s
+    r.update({
+        "formula": "max(n*bytes_per_key/HBM, n*t*(k-1)*polys/PEAK_mul128) / kernel time, "
+                   "n = every key of the launch",
+        "roofline_ms": max(hbm_s, mul_s) * 1e3, "hbm_leg_ms": hbm_s * 1e3, "mul_leg_ms": mul_s * 1e3,
+        "kernel_ms": kern_s * 1e3, "mul128_per_key": mul_per_key, "bytes_per_key": bytes_per_key,
+        "peak_source": "ms_probe_mul128 variant 0 (independent 64x64->128 products, low half by "
+                       "multiplication, high half by __umul64hi, every SM), measured in this run; "
+                       "HBM: " + hbm_src,
+        "hbm": {"achieved_gbs": n * bytes_per_key / kern_s / 1e9, "peak_gbs": hbm_gbs,
+                "frac": n * bytes_per_key / kern_s / 1e9 / hbm_gbs},
+    })
+    return r
+
+
+def imad_fraction(entries: int, t: int, nf: int, kern_s: float, peaks: dict) -> dict:
+    """Counted mad.wide per hashed entry at the measured 32x32->64 multiply-add rate."""
+    per = mad_wide_per_entry(t, nf)
+    rate = entries * per / kern_s
+    return {"mad_wide_per_entry": per, "entries_per_launch": entries,
+            "achieved_per_s": rate, "peak_per_s": peaks["mad_wide_per_s"],
+            "frac": rate / peaks["mad_wide_per_s"],
+            "peak_source": "ms_probe_mul128 variants 1 and 4 (mad.wide.u32: 8 dependent chains, "
+                           "and 16 cross-coupled chains per thread), the larger, measured in this "
+                           "run"}
+
+
 # ------------------------------------------------------------------ cpu baseline
 
 def cpu_baseline(wl: dict, seed: int, target_s: float, gpu_check=None) -> dict:
@@ -195,6 +269,118 @@ def cpu_baseline(wl: dict, seed: int, target_s: float, gpu_check=None) -> dict:
 
 # ------------------------------------------------------------------ our arm
 
+def time_steps(ms, sk, keys, w, f2_out, steps: int, warmup: int, gpu_index: int, stream,
+               barrier=None) -> dict:
+    """Device time of `steps` steps (zero, update, F2) after `warmup`, with CUDA
+    events on the launching stream around every update kernel, and the SM
+    clocks sampled during the timed region.  Inputs smaller than twice the L2
+    get a 512 MiB write before every timed step; only the steps are timed, and
+    a step is one CUDA-graph replay (three short kernels, which eager launches
+    would leave host-bound)."""
+    import torch
+    n = keys.numel() if keys.dtype != torch.int32 else keys.numel()
+    bytes_per_key = 8 + (4 if w is not None else 0)
+    dev = keys.device
+    l2_bytes = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 129 << 20)
+    small = n * bytes_per_key < 2 * l2_bytes
+
+    def step():
+        sk.reset()
+        sk.update(keys, w)
+        sk.estimate_f2(out=f2_out)
+
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev) if small else None
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(steps):
+        if small:
+            flush.fill_(i & 255)
+        sk.reset()
+        ev[i][0].record(stream)
+        sk.update(keys, w)
+        ev[i][1].record(stream)
+        sk.estimate_f2(out=f2_out)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    ms_total = t_start.elapsed_time(t_end)
+    kern_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)]
+    if small:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        for _ in range(max(3, warmup)):
+            graph.replay()
+        sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 255)
+            sev[i][0].record(stream)
+            graph.replay()
+            sev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms_total = sum(sev[i][0].elapsed_time(sev[i][1]) for i in range(steps))
+    if barrier:
+        barrier()
+    clk = clocks.stop()
+    del flush
+    return {"ms_total": ms_total, "kern_ms": kern_ms, "small": small, "clocks": clk,
+            "bytes_per_key": bytes_per_key}
+
+
+def hashed_entries(sk, keys, w) -> int:
+    """Entries one launch hashes (keys with a non-zero weight, or with the
+    de-duplication table the distinct (block, key) entries): one untimed update
+    with the library's statistics hook on."""
+    import torch
+    hashed_t = torch.zeros(1, dtype=torch.int64, device=keys.device)
+    sk.set_stats(hashed_t)
+    sk.reset()
+    sk.update(keys, w)
+    torch.cuda.synchronize()
+    sk.set_stats(None)
+    return int(hashed_t.item())
+
+
+def plain_2p28_result(args, ms, peaks, hbm_gbs, hbm_src) -> dict:
+    """The plain distribution (uniform keys below p, weights in [-100, 100], t=5,
+    m=1024) at 2^28 keys, where the hot-path target is judged."""
+    import torch
+    wl = WORKLOADS["plain-2^28"]
+    n, t, m = wl["n"], wl["t"], wl["m"]
+    keys_np, w_np = make_inputs(wl, args.seed, 0)
+    keys = torch.from_numpy(keys_np.view(np.int64)).cuda()
+    w = torch.from_numpy(w_np).cuda()
+    del keys_np, w_np
+    sk = ms.Sketch(t=t, m=m, k=4, b=61, c=1, seed=args.seed, mode=0)
+    f2_out = torch.empty(2, dtype=torch.int64, device="cuda")
+    steps = max(10, min(args.steps, 60))
+    r = time_steps(ms, sk, keys, w, f2_out, steps, args.warmup, 0,
+                   torch.cuda.current_stream())
+    kern_s = statistics.mean(r["kern_ms"]) * 1e-3
+    roof = roofline_8d(n, t, 1, 12, kern_s, peaks, hbm_gbs, hbm_src)
+    roof["imad"] = imad_fraction(n, t, 1, kern_s, peaks)
+    roof["traffic"] = MEASURED_TRAFFIC_PER_KEY.get("plain-2^28", 0) * n or None
+    out = {"workload": wl["desc"] + " (2^28 keys, t=5, m=1024, weights in [-100,100])",
+           "value": n * steps / (r["ms_total"] * 1e-3), "unit": "keys/s",
+           "ms_per_step": r["ms_total"] / steps, "steps": steps, "roofline": roof,
+           "launch": sk.last_launch(), "f2_estimate": str(ms.u128_to_int(f2_out.cpu()))}
+    if r["clocks"]:
+        out["clocks"] = r["clocks"]
+    del keys, w, sk
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, wl):
     import torch
     import torch.distributed as dist
@@ -211,70 +397,18 @@ def run_ours(args, wl):
     stream = torch.cuda.current_stream(dev)
 
     n, t, m, mode = wl["n"], wl["t"], wl["m"], wl["mode"]
+    nf = 2 if mode == 1 else 1
     keys_np, w_np = make_inputs(wl, args.seed, rank)
     keys = torch.from_numpy(keys_np.view(np.int64)).to(dev)
     w = None if w_np is None else torch.from_numpy(w_np).to(dev)
     sk = ms.Sketch(t=t, m=m, k=4, b=61, c=1, seed=args.seed, mode=mode)
     f2_out = torch.empty(2, dtype=torch.int64, device=dev)
 
-    def step():
-        sk.reset()
-        sk.update(keys, w)
-        sk.estimate_f2(out=f2_out)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
+    barrier = dist.barrier if world > 1 else None
+    r = time_steps(ms, sk, keys, w, f2_out, args.steps, args.warmup, local, stream, barrier)
     launch = sk.last_launch()
-
-    # device-timed steps, with per-step events around the update kernel.  Inputs
-    # larger than twice the L2 stream through it (no flush needed); smaller ones
-    # (the 2^20-key plain sketch: 12 MiB) get a 512 MiB write before every
-    # timed step, only the steps are timed, and a step is one CUDA-graph replay
-    # (three short kernels: launch overhead would otherwise dominate).
-    bytes_per_key = 8 + (4 if w is not None else 0)
-    l2_bytes = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 129 << 20)
-    small = n * bytes_per_key < 2 * l2_bytes
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev) if small else None
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for i in range(args.steps):
-        if small:
-            flush.fill_(i & 255)
-        sk.reset()
-        ev[i][0].record(stream)
-        sk.update(keys, w)
-        ev[i][1].record(stream)
-        sk.estimate_f2(out=f2_out)
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    ms_total = t_start.elapsed_time(t_end)
-    kern_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
-    if small:
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            step()
-        for _ in range(max(3, args.warmup)):
-            graph.replay()
-        sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.fill_(i & 255)
-            sev[i][0].record(stream)
-            graph.replay()
-            sev[i][1].record(stream)
-        torch.cuda.synchronize()
-        ms_total = sum(sev[i][0].elapsed_time(sev[i][1]) for i in range(args.steps))
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
+    ms_total, kern_ms, small, clk = r["ms_total"], r["kern_ms"], r["small"], r["clocks"]
+    bytes_per_key = r["bytes_per_key"]
     if world > 1:
         tt = torch.tensor([ms_total], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -311,20 +445,10 @@ def run_ours(args, wl):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
     assert ms.u128_to_int(f2_h) == f2_est
+    del keys_h, w_h
 
-    # integer-multiply peaks on this GPU: 64x64->128 products (the roofline's
-    # denominator) and 32x32->64 multiply-adds (context)
-    mul_rate, _ = ms.probe_mul128(variant=0, iters=1 << 12)
-    imad_rate, _ = ms.probe_mul128(variant=1, iters=1 << 13)
-    # entries one launch hashes (keys, or with the de-duplication table the
-    # distinct (block, key) entries): one untimed update with the stats hook on
-    hashed_t = torch.zeros(1, dtype=torch.int64, device=dev)
-    sk.set_stats(hashed_t)
-    sk.reset()
-    sk.update(keys, w)
-    torch.cuda.synchronize()
-    sk.set_stats(None)
-    hashed = int(hashed_t.item())
+    peaks = probe_peaks(ms)
+    hashed = hashed_entries(sk, keys, w)
     global_counters = launch.get("place") in (2, 3)
     red_rate = None
     if global_counters:
@@ -340,54 +464,27 @@ def run_ours(args, wl):
 
     value = world * n * args.steps / (ms_total * 1e-3)
     kern_avg_s = statistics.mean(kern_ms) * 1e-3
-    mul128_per_key = t * 3 * (2 if mode == 1 else 1)
-    # the integer work the launch executes: t(k-1) (or 2t(k-1)) mul128 per hashed entry
-    achieved_mul = hashed * mul128_per_key / kern_avg_s
-    peak_mul = mul_rate
-    hbm_peak = 6787.9
-    try:
-        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
-    except (OSError, KeyError, ValueError):
-        pass
-    alu = {
-        "achieved": achieved_mul / 1e9,
-        "peak": peak_mul / 1e9,
-        "unit": "Gmul128/s",
-        "frac": achieved_mul / peak_mul,
-        "mul128_per_hashed_entry": mul128_per_key,
-        "peak_source": "ms_probe_mul128 variant 0: independent 64x64->128 products "
-                       "(low half by multiplication, high half by __umul64hi), 8 chains per "
-                       "thread on every SM, measured in this run",
-        "probe_mad_wide_32x32_per_s": imad_rate,
-    }
+    hbm_gbs, hbm_src = hbm_peak_gbs()
+    roofline = roofline_8d(n, t, nf, bytes_per_key, kern_avg_s, peaks, hbm_gbs, hbm_src)
+    roofline["imad"] = imad_fraction(hashed, t, nf, kern_avg_s, peaks)
+    roofline["imad"]["note"] = ("entries = what the launch hashed (with the de-duplication table, "
+                                "the distinct (block, key) entries with their counts)")
     if global_counters:
         adds = hashed * t / kern_avg_s  # counter additions (one per row per hashed entry)
-        roofline = {
-            "bound": "l2_atomic",
-            "achieved": adds / 1e9,
-            "peak": red_rate / 1e9,
-            "unit": "Gadd/s",
+        roofline["l2_atomic"] = {
+            "achieved": adds / 1e9, "peak": red_rate / 1e9, "unit": "Gadd/s",
             "frac": adds / red_rate,
             "peak_source": "ms_probe_red: scattered red.global.add.s32 into an L2-resident "
-                           "buffer the size of the replicas, every SM, measured in this run",
-            "alu": alu,
-        }
-    else:
-        roofline = {"bound": "alu"}
-        roofline.update({k: alu[k] for k in ("achieved", "peak", "unit", "frac")})
-        roofline.update({k: alu[k] for k in ("mul128_per_hashed_entry", "peak_source",
-                                             "probe_mad_wide_32x32_per_s")})
+                           "buffer the size of the replicas, every SM, measured in this run"}
     roofline.update({
         "traffic": (MEASURED_TRAFFIC_PER_KEY[args.workload] * n
                     if args.workload in MEASURED_TRAFFIC_PER_KEY else None),
         "traffic_unit": "bytes per launch (ncu DRAM bytes of a 2^25-key capture, scaled)",
         "algorithmic_bytes": n * bytes_per_key,
         "kernel": "k_cs_update",
-        "kernel_ms": statistics.mean(kern_ms),
         "keys_per_launch": n,
         "hashed_entries_per_launch": hashed,
-        "hbm": {"achieved_gbs": n * bytes_per_key / kern_avg_s / 1e9, "peak_gbs": hbm_peak,
-                "frac": n * bytes_per_key / kern_avg_s / 1e9 / hbm_peak},
+        "probes": peaks,
     })
     line = {
         "metric": "Count Sketch key updates/s (k=4, p=2^61-1)",
@@ -429,6 +526,13 @@ def run_ours(args, wl):
             return (np.array_equal(s2.counters().cpu().numpy(), C_oracle)
                     and s2.f2() == f2_oracle)
         line["cpu_baseline"] = cpu_baseline(wl, args.seed, args.cpu_seconds, gpu_check)
+    if world == 1 and not args.no_extra and args.workload == "large" and args.keys == 0:
+        # the other two figures of the metric ("% roofline; batched vs plain"),
+        # each timed with its own clock record
+        del keys, w, sk
+        torch.cuda.empty_cache()
+        line["plain_2p28"] = plain_2p28_result(args, ms, peaks, hbm_gbs, hbm_src)
+        line["batched"] = batched_result(args, ms, peaks)
     if world > 1:
         dist.destroy_process_group()
     return line
@@ -669,13 +773,14 @@ def run_table1(args):
                                        "p=2^89-1,k=4": [65.7, 68.7, 85.2]})
 
 
-def run_batched(args):
+def batched_result(args, ms, peaks=None) -> dict:
     """Batched: independent sketches (t=5, m from {256, 1024, 4096, 8192}, own
     seeds, n_i = floor(10^(3+4U)) keys below 2^61-1, int32 weights in [-100, 100])
-    in one persistent graph-captured launch, against one cs_update per sketch."""
+    in one persistent graph-captured launch, against one cs_update per sketch.
+    The tuner picks the launch configuration for the whole plan, and once more
+    for the sketches of each width class alone."""
     import torch
     import oracle
-    import paper_2008_08654_gb300 as ms
     S = args.sketches
     u = datagen.unit_doubles(args.seed, S, datagen.STREAM_LENGTHS)
     ns = np.floor(10.0 ** (3.0 + 4.0 * u)).astype(np.int64)
@@ -700,23 +805,39 @@ def run_batched(args):
         for chunk in (1 << 15, 1 << 17, 1 << 19):
             for ratio in (2, 8, 32):
                 cands.append({"threads": threads, "chunk_keys": chunk, "smem_min_ratio": ratio})
+    per_m = {}
     if args.no_tune:
-        best, times, cands = ms.default_tuning().as_dict(), [], []
+        best, times, ncand = ms.default_tuning().as_dict(), [], 0
     else:
         best, times = ms.tune_batched(jobs, cands, reps=2)
+        ncand = len(cands)
+        for mc in (256, 1024, 4096, 8192):
+            sub = [j for j, wd in zip(jobs, widths) if wd == mc]
+            if not sub:
+                continue
+            b_m, t_m = ms.tune_batched(sub, cands, reps=2)
+            keys_m = int(sum(j[1].numel() for j in sub))
+            per_m[str(mc)] = {"sketches": len(sub), "keys": keys_m, "choice": b_m,
+                              "best_ms": min(t_m) if t_m else None,
+                              "keys_per_s": keys_m / (min(t_m) * 1e-3) if t_m else None}
     plan = ms.Batch(jobs, best)
 
     def reset_all():
         for sk in sketches:
             sk.reset()
-    reset_all()
-    t_graph = _timed(plan.launch, max(1, args.steps), args.warmup)
-    t_direct = _timed(plan.launch_direct, max(1, args.steps), 1)
 
     def plain():
         for sk, kk, ww in jobs:
             sk.update(kk, ww)
-    t_plain = _timed(plain, max(1, min(args.steps, 5)), 1)
+
+    reset_all()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    t_graph = _timed(plan.launch, max(3, args.steps), max(3, args.warmup))
+    t_direct = _timed(plan.launch_direct, max(3, args.steps), 3)
+    t_plain = _timed(plain, max(3, min(args.steps, 5)), 3)
+    clk = clocks.stop()
     # parity of a sample of sketches after one clean batched launch
     reset_all()
     plan.launch()
@@ -734,16 +855,34 @@ def run_batched(args):
                                 kh, wh, nthreads=os.cpu_count() or 1)
         ok = ok and np.array_equal(sk.counters().cpu().numpy(), want)
     info = plan.info()
-    return _line("batched Count Sketch key updates/s (k=4, p=2^61-1, t=5)", total / (t_graph * 1e-3),
-                 "keys/s", args,
-                 {"workload": "%d sketches, %d keys in total (log-uniform 1e3..1e7 per sketch)"
-                  % (S, total), "m_classes": {str(m): int((widths == m).sum()) for m in
-                                                (256, 1024, 4096, 8192)}},
-                 ms_per_step=t_graph, direct_launch_keys_per_s=total / (t_direct * 1e-3),
-                 plain_launches_keys_per_s=total / (t_plain * 1e-3),
-                 speedup_vs_plain_launches=t_plain / t_graph, tuner_choice=best,
-                 tuner_candidates=len(cands), tuner_times_ms=times, plan=info,
-                 parity_on_sample=bool(ok))
+    out = {"workload": "%d sketches, %d keys in total (log-uniform 1e3..1e7 per sketch), t=5, "
+                       "m uniform over {256, 1024, 4096, 8192}, weights in [-100, 100]"
+                       % (S, total),
+           "value": total / (t_graph * 1e-3), "unit": "keys/s", "ms_per_step": t_graph,
+           "keys": total,
+           "m_classes": {str(mc): int((widths == mc).sum()) for mc in (256, 1024, 4096, 8192)},
+           "direct_launch_keys_per_s": total / (t_direct * 1e-3),
+           "plain_launches_keys_per_s": total / (t_plain * 1e-3),
+           "plain_launches_ms": t_plain,
+           "speedup_vs_plain_launches": t_plain / t_graph, "tuner_choice": best,
+           "tuner_choice_per_m": per_m, "tuner_candidates": ncand, "tuner_times_ms": times,
+           "plan": info, "parity_on_sample": bool(ok),
+           "gpu_launches_per_step": 2}
+    if peaks:
+        out["mul128_frac"] = total * 15 / (t_graph * 1e-3) / peaks["mul128_per_s"]
+    if clk:
+        out["clocks"] = clk
+    del plan, jobs, sketches, keys, wts
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    import paper_2008_08654_gb300 as ms
+    r = batched_result(args, ms, probe_peaks(ms))
+    extra = {k: v for k, v in r.items() if k not in ("workload", "value", "unit")}
+    return _line("batched Count Sketch key updates/s (k=4, p=2^61-1, t=5)", r["value"], "keys/s",
+                 args, {"workload": r["workload"], "m_classes": r["m_classes"]}, **extra)
 
 
 def run_serving(args):
@@ -762,19 +901,30 @@ def run_serving(args):
     # reads each request's keys in place over the host link
     pool = torch.from_numpy(datagen.zipf(args.seed, 1.1, 1 << 32, 1 << 26).view(np.int64))
     pool = pool.pin_memory()
-    count = max(200, args.keys or 4000)
+    # 2e5 requests per run (each of the 10^4 sketches about 20 times): windows
+    # of more than a second at every offered load
+    count = max(200, args.keys or 200000)
     qf, lo, hi = 0.1, 256, 1 << 20
     mean_n = (hi - lo) / math.log(hi / lo)
-    srv.run_load(pool, count=200, rate_per_s=1e6, query_fraction=qf, min_keys=lo, max_keys=hi,
+    srv.run_load(pool, count=2000, rate_per_s=1e6, query_fraction=qf, min_keys=lo, max_keys=hi,
                  seed=args.seed + 99)  # warm-up
-    peak = srv.run_load(pool, count=count, rate_per_s=1e7, query_fraction=qf, min_keys=lo,
-                        max_keys=hi, seed=args.seed)
+
+    def measured(rate, seed):
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.3)
+        r = srv.run_load(pool, count=count, rate_per_s=rate, query_fraction=qf, min_keys=lo,
+                         max_keys=hi, seed=seed)
+        clk = clocks.stop()
+        if clk:
+            r["clocks"] = clk
+        return r
+
+    peak = measured(1e7, args.seed)
     levels = {}
     for frac in (0.5, 0.8, 0.95):
         rate = frac * peak["keys_per_s"] / ((1 - qf) * mean_n)
-        levels["%d%%" % int(frac * 100)] = srv.run_load(
-            pool, count=count, rate_per_s=rate, query_fraction=qf, min_keys=lo, max_keys=hi,
-            seed=args.seed + int(frac * 100))
+        levels["%d%%" % int(frac * 100)] = measured(rate, args.seed + int(frac * 100))
     srv.close()
     return _line("served Count Sketch key updates/s (k=4, p=2^61-1, t=5)", peak["keys_per_s"],
                  "keys/s", args,
@@ -782,7 +932,8 @@ def run_serving(args):
                               "run, 10%% F2 queries, updates of log-uniform 256..2^20 Zipf(1.1) "
                               "keys from a page-locked host pool of 2^26 keys (512 MiB), read in place by "
                               "the update kernel; 40 GB staging" % (S, count)},
-                 saturated=peak, offered_load=levels)
+                 saturated=peak, offered_load=levels,
+                 **({"clocks": peak["clocks"]} if "clocks" in peak else {}))
 
 
 EXTRA = {"sweep": run_sweep, "div": run_div, "divwide": run_divwide, "table1": run_table1,

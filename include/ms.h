@@ -64,6 +64,18 @@ const char* ms_last_cuda_error(void);
 /* Library version, e.g. "1.0.0". */
 const char* ms_version(void);
 
+/*
+ * ms_set_tracing -- NVTX ranges (a tracing aid, not in the paper) around the
+ * library's compute and transfer entry points (hashing, division, sketch
+ * update / F2 / point query / merge / reset / export / import, batched
+ * launches and tuning, server submissions, drain and load runs), named after
+ * the call.  Off by default; MS_NVTX=1 in the environment turns it on when the
+ * library first checks.  The ranges go to a profiler that injects NVTX (Nsight
+ * Systems, Nsight Compute) and cost nothing otherwise; the library needs no
+ * NVTX library at run time.  on: 0 or 1.  Returns the previous setting.
+ */
+int ms_set_tracing(int on);
+
 /* ------------------------------------------------------------------ hashing */
 
 typedef struct ms_hash ms_hash;
@@ -266,7 +278,10 @@ ms_status cs_estimate_f2(const cs_sketch* sk, ms_u128* out_dev, ms_u128* rows_de
  *  sums and a ticket), which every GPU that loads the library holds until the
  *  process exits.  The first call on a device looks up that array's device
  *  address (once per device, with that device current); make that first call
- *  before any stream capture begins.  Each call first clears the ticket on
+ *  before any stream capture begins.  The address stays cached for the life of
+ *  the process: after a cudaDeviceReset of that device it is stale, as is
+ *  every sketch handle made before it, so do not call into the library on a
+ *  device after resetting it.  Each call first clears the ticket on
  *  `stream`.  All calls share the one array, so calls that overlap on the GPU
  *  (for example on two streams) race and give wrong results: keep them ordered
  *  on one stream.
@@ -320,19 +335,28 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  *  strategy: 0 = Horner per row (Algorithm Mersenne), 1 = powers of x once per
  *            key, then sum a_i x^i per row (k = 4 with t = 5 or 7, every prime;
  *            for the other primes only with a power-of-two m; other sketches
- *            use Horner).  Both give identical hash values.
+ *            use Horner); 2 = the power sum as 1, but for 2^61-1 with a
+ *            shared-memory tile in the general kernel (four keys a thread)
+ *            instead of the lean one (one key a thread; the default there).
+ *            All give identical hash values.
  *  threads (multiple of 32, <= 512; default 512, 256 for place 1), blocks
  *  (total), blocks_per_sm (cap), cluster (power of two <= 16, place 1 only),
  *  replicas (power of two <= 32, place 2 only; capped at the replicas the
  *  sketch owns; default 16),
- *  aggregate (0, 1 or 2, default 2; unit weights and place 2 or 3 only):
+ *  aggregate (0 to 3, default 3; unit weights and place 2 or 3 only):
  *  1 = lanes of a warp holding the same key send one update carrying their
  *  count; 2 = a per-block table of 4096 keys in shared memory (one-word keys:
  *  every prime but 2^89-1): a key the table holds is only counted, and is
  *  hashed once, with its count, when the block ends; the other keys are hashed
  *  128 at a time from a per-warp queue.  A warp whose table takes under 1/8 of
- *  the keys of its 17th to 32nd chunks of 128 stops using it.  The counters are
- *  identical for every setting (a sketch is linear in the stream).
+ *  the keys of its 17th to 32nd chunks of 128 stops using it.  3 = as 2, and a
+ *  key the block's table misses is counted in a second-level table of 2^21
+ *  keys in global memory (24 MiB, allocated by the sketch on first use and
+ *  kept, L2-resident) when it owns or can claim its slot there; after the
+ *  update one kernel hashes each key that table holds once, with its count,
+ *  and empties it.  The default uses the second level for streams of at least
+ *  2^22 keys (3 forces it for any length).  The counters are identical for
+ *  every setting (a sketch is linear in the stream).
  * Errors: INVALID_ARG.
  */
 ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int threads, int blocks,
@@ -351,7 +375,8 @@ ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int threads, int
 ms_status cs_set_stats(cs_sketch* sk, uint64_t* hashed_dev);
 
 /* The configuration the most recent cs_update on this sketch launched with;
- * `specialized` is 1 when a compile-time (t, k) kernel served it.  Any output
+ * `specialized` is 1 when a compile-time (t, k) kernel served it, 2 when that
+ * was the lean one-key-a-thread shared-memory-tile kernel.  Any output
  * pointer may be NULL. */
 ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* threads, int* blocks,
                          int* cluster, int* smem, int* specialized, int* replicas);
@@ -372,6 +397,9 @@ ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strategy, int* th
  *             result, so the product cannot be hoisted out of the loop.
  *  variant 2: one dependent 32-bit multiply-add (low word only).
  *  variant 3: one 32-bit integer add (two dependent adds per step, both counted).
+ *  variant 4: one 32x32->64 multiply-add (mad.wide.u32) whose multiplicand is
+ *             another accumulator's latest value, sixteen accumulators per thread
+ *             in cross-coupled pairs (throughput, not latency).
  */
 ms_status ms_probe_mul128(int variant, int iters, uint64_t* sink_dev, double* rate, double* ms);
 

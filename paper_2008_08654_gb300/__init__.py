@@ -67,6 +67,7 @@ def _load():
         "ms_status_str": (ctypes.c_char_p, [i]),
         "ms_last_cuda_error": (ctypes.c_char_p, []),
         "ms_version": (ctypes.c_char_p, []),
+        "ms_set_tracing": (ctypes.c_int, [ctypes.c_int]),
         "ms_hash_init": (i, [pp, i, i, u64, u64]),
         "ms_hash_init_coeffs": (i, [pp, i, i, u64, vp]),
         "ms_hash_coeffs": (i, [vp, vp]),
@@ -185,6 +186,12 @@ def _u128_array(values):
 
 def version() -> str:
     return _load().ms_version().decode()
+
+
+def set_tracing(on: bool) -> bool:
+    """NVTX ranges around the library's entry points (ms_set_tracing); returns
+    the previous setting."""
+    return bool(_load().ms_set_tracing(1 if on else 0))
 
 
 # ------------------------------------------------------------------ hashing

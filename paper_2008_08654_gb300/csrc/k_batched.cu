@@ -19,10 +19,10 @@
 
 namespace msk {
 
-struct PsCoef {  // one polynomial, Karatsuba power-sum form (p = 2^61-1, k = 4)
-    u64 a0;
-    u32 lo[3], hi[3];
-    int nd[3];  // lo - hi
+struct PsCoef {  // one polynomial, signed-digit power-sum form (p = 2^61-1, k = 4; row_sd)
+    u64 k1;
+    int cl[3], ch[3];
+    int nd[3];  // cl - ch
     u32 pad;
 };
 
@@ -84,15 +84,8 @@ __global__ void __launch_bounds__(1024) k_cs_update_batched(const BatchArgs a) {
         for (int i = threadIdx.x; i < nw; i += blockDim.x) scoef[i] = src[i];
         if (PS) {
             for (int f = threadIdx.x; f < (r1 - r0) * NF; f += blockDim.x) {
-                const u64* c = src + (size_t)f * 4;
                 PsCoef pc;
-                pc.a0 = c[0];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    pc.lo[i] = (u32)(c[i + 1] & 0x7FFFFFFFull);
-                    pc.hi[i] = (u32)(c[i + 1] >> 31);
-                    pc.nd[i] = (int)pc.lo[i] - (int)pc.hi[i];
-                }
+                msf::P61::sd_coef(src + (size_t)f * 4, pc.cl, pc.ch, pc.nd, pc.k1);
                 pc.pad = 0;
                 sps[f] = pc;
             }
@@ -124,13 +117,13 @@ __global__ void __launch_bounds__(1024) k_cs_update_batched(const BatchArgs a) {
                     auto row = [&](int r) {
                         const PsCoef cb = sps[(r - r0) * NF];
                         u32 ylo, yhi, bucket, sb;
-                        msf::P61::row_kara(xp, cb.lo, cb.hi, cb.nd, cb.a0, a.c2p31, a.c4, ylo, yhi);
-                        msf::P61::bucket_sign_hl(ylo, yhi, mask, bucket, sb);
+                        msf::P61::row_sd(xp, cb.cl, cb.ch, cb.nd, cb.k1, a.c2p31, a.c4, ylo, yhi);
+                        msf::P61::bucket_sign_sd(ylo, yhi, mask, bucket, sb);
                         if (MODE == CS_TWO_POLY) {
                             const PsCoef cs = sps[(r - r0) * NF + 1];
                             u32 unused;
-                            msf::P61::row_kara(xp, cs.lo, cs.hi, cs.nd, cs.a0, a.c2p31, a.c4, ylo, yhi);
-                            msf::P61::bucket_sign_hl(ylo, yhi, mask, unused, sb);
+                            msf::P61::row_sd(xp, cs.cl, cs.ch, cs.nd, cs.k1, a.c2p31, a.c4, ylo, yhi);
+                            msf::P61::bucket_sign_sd(ylo, yhi, mask, unused, sb);
                         }
                         batched_add(tile, job.counters, r, r0, log2m, bucket, sb, wt[q], big[q]);
                     };

@@ -299,6 +299,7 @@ extern "C" int ms_div_wide_steps(int b, uint64_t c) {
 
 extern "C" ms_status ms_div_wide(int b, uint64_t c, const uint64_t* v_dev, uint64_t* q_dev,
                                  uint64_t* r_dev, size_t n, void* stream) {
+    msi::TraceRange trace_("ms_div_wide");
     if (b < 32 || b > 1024 || c < 1 || c >= (1ull << 32) || (c > 1 && (uint64_t)b <= 64 &&
                                                               c >= (1ull << (b / 2))))
         return MS_ERR_INVALID_ARG;

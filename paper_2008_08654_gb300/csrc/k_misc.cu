@@ -167,6 +167,15 @@ cudaError_t launch_cs_update(int prime, const UpdateArgs& a, const u64* coef_hos
     }
 }
 
+cudaError_t launch_gtable_drain(int prime, const UpdateArgs& a, cudaStream_t stream) {
+    switch (prime) {
+        case PRIME_31: return launch_gtable_drain_p31(a, stream);
+        case PRIME_61: return launch_gtable_drain_p61(a, stream);
+        case PRIME_89: return launch_gtable_drain_p89(a, stream);
+        default: return launch_gtable_drain_p64(a, stream);
+    }
+}
+
 cudaError_t query_cs_update_occupancy(int prime, const UpdateArgs& a, const u64* coef_host,
                                       const LaunchCfg& cfg, int* result) {
     *result = 0;
@@ -495,6 +504,11 @@ cudaError_t launch_divmod(int prime, const ms_u128* v, ms_u128* q, void* r, u64 
 //             cannot hoist the product out of the loop
 //  variant 2: x <- x*b + y (mad.lo.u32): one dependent 32-bit multiply-add
 //  variant 3: x <- x + y; y <- y + x (add.u32): two dependent 32-bit adds
+//  variant 4: a <- lo32(c)*b + a, c <- lo32(a)*b + c (mad.wide.u32) on eight
+//             pairs of accumulators per thread: each multiplicand is the other
+//             accumulator's latest value, so no product can be hoisted, and the
+//             sixteen chains per thread measure the multiplier's throughput
+//             rather than its latency
 __global__ void __launch_bounds__(256) k_probe(int variant, int iters, u64 seed, u64* sink) {
     u64 a[8], wv[8];
     u32 x[8], y[8];
@@ -524,7 +538,7 @@ __global__ void __launch_bounds__(256) k_probe(int variant, int iters, u64 seed,
             for (int c = 0; c < 8; ++c)
                 asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[c]) : "r"(b32), "r"(y[c]));
         }
-    } else {
+    } else if (variant == 3) {
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -532,6 +546,19 @@ __global__ void __launch_bounds__(256) k_probe(int variant, int iters, u64 seed,
                 asm volatile("add.u32 %0, %0, %1;" : "+r"(y[c]) : "r"(x[c]));
             }
         }
+    } else {
+        u64 acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = wv[c] ^ 0xAAAAull;
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(wv[c]) : "r"((u32)acc[c]), "r"(b32));
+                asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[c]) : "r"((u32)wv[c]), "r"(b32));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) wv[c] ^= acc[c];
     }
     u64 s = 0;
 #pragma unroll
@@ -565,7 +592,8 @@ cudaError_t run_probe_mul128(int variant, int iters, u64* sink, double* rate, do
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const double ops = (double)blocks * 256.0 * 8.0 * (double)iters * (variant == 3 ? 2.0 : 1.0);
+    const double ops = (double)blocks * 256.0 * 8.0 * (double)iters *
+                       ((variant == 3 || variant == 4) ? 2.0 : 1.0);
     *ms = t;
     *rate = ops / (t * 1e-3);
     return cudaSuccess;

@@ -165,10 +165,14 @@ struct PsLimbs {
 
 template <class F, int NFUN, int K>
 struct ParamCoef {
+    static constexpr int SD = (NFUN > 0 && K == 4 && std::is_same<F, msf::P61>::value) ? NFUN : 0;
     u64 w[NFUN > 0 ? NFUN * K * FieldOps<F>::WORDS : 1];
-    u32 lo[NFUN > 0 ? NFUN * K : 1];  // P61 only: a & (2^31-1)
-    u32 hi[NFUN > 0 ? NFUN * K : 1];  // P61 only: a >> 31
-    int nd[NFUN > 0 ? NFUN * K : 1];  // P61 only: lo - hi
+    // P61, k = 4 (row_sd): signed digits of a1..a3 of function f at [3f + i - 1],
+    // cl - ch, and the row constant K + 1
+    int cl[SD > 0 ? 3 * SD : 1];
+    int ch[SD > 0 ? 3 * SD : 1];
+    int nd[SD > 0 ? 3 * SD : 1];
+    u64 k1[SD > 0 ? SD : 1];
     u32 ps[(NFUN > 0 && K == 4 && PsLimbs<F>::N > 0) ? NFUN * PsLimbs<F>::N : 1];  // P89, P64
     u32 c2p31, c4;                    // 2^31 and 4, as run-time operands
 };
@@ -315,6 +319,24 @@ __device__ __forceinline__ bool dedup_count(u64* tk, int* tc, int log2slots, u64
     return true;
 }
 
+// Second-level table in global memory (L2-resident): counts c occurrences of
+// `key` when its slot holds it or was free (claimed here); false otherwise.
+// `cur` is the slot's key as loaded before (so that a warp's loads overlap).
+__device__ __forceinline__ u32 gtable_slot(u64 key, int glog2) {
+    return (u32)((key * 0xD6E8FEB86659FD93ull) >> (64 - glog2));
+}
+__device__ __forceinline__ bool gtable_count(unsigned long long* gk, int* gc, u32 slot, u64 key,
+                                             u64 cur, int c) {
+    if (key == DEDUP_EMPTY) return false;
+    if (cur == DEDUP_EMPTY) {
+        cur = atomicCAS(gk + slot, DEDUP_EMPTY, (unsigned long long)key);
+        if (cur == DEDUP_EMPTY) cur = key;  // claimed by this thread
+    }
+    if (cur != key) return false;
+    atomicAdd(gc + slot, c);
+    return true;
+}
+
 // ------------------------------------------------------------ cluster helpers
 
 __device__ __forceinline__ u32 cluster_rank() {
@@ -391,36 +413,30 @@ __device__ __forceinline__ void apply_fast(int* tile, u32 tile_saddr, long long*
     }
 }
 
-// Bucket and sign bit of row r for p = 2^61-1, k = 4 (Karatsuba power sum):
-// two-for-one (both from one polynomial) or two polynomials (the sign from the
-// second one's bit 60).
+// Bucket and sign bit of row r for p = 2^61-1, k = 4 (signed-digit power sum,
+// row_sd): two-for-one (both from one polynomial) or two polynomials (the sign
+// from the second one's bit 60).
 template <int NF, bool ANY = false, class PC>
 __device__ __forceinline__ void p61_row_bs(const msf::P61::Pow3& xp, const PC& pc, int r, u32 mask,
                                            u32 arb_r, u32& bucket, u32& sign) {
     typedef msf::P61 F;
     const int fb = r * NF;
     u32 ylo, yhi;
-    {
-        const u32 al[3] = {pc.lo[fb * 4 + 1], pc.lo[fb * 4 + 2], pc.lo[fb * 4 + 3]};
-        const u32 ah[3] = {pc.hi[fb * 4 + 1], pc.hi[fb * 4 + 2], pc.hi[fb * 4 + 3]};
-        const int nd[3] = {pc.nd[fb * 4 + 1], pc.nd[fb * 4 + 2], pc.nd[fb * 4 + 3]};
-        F::row_kara(xp, al, ah, nd, pc.w[fb * 4], pc.c2p31, pc.c4, ylo, yhi);
-    }
+    F::row_sd(xp, pc.cl + 3 * fb, pc.ch + 3 * fb, pc.nd + 3 * fb, pc.k1[fb], pc.c2p31, pc.c4, ylo,
+              yhi);
     if (ANY) {  // Algorithm Mersenne-arb-r on the canonical value
         u32 a;
-        F::arb_split(F::canon_hl(ylo, yhi), arb_r, bucket, a);
+        F::arb_split(F::canon_sd(ylo, yhi), arb_r, bucket, a);
         sign = a ^ 1u;  // s = 2a - 1: subtract when a = 0
     } else {
-        F::bucket_sign_hl(ylo, yhi, mask, bucket, sign);
+        F::bucket_sign_sd(ylo, yhi, mask, bucket, sign);
     }
     if (NF == 2) {
         const int fs = fb + 1;
-        const u32 sl[3] = {pc.lo[fs * 4 + 1], pc.lo[fs * 4 + 2], pc.lo[fs * 4 + 3]};
-        const u32 sh[3] = {pc.hi[fs * 4 + 1], pc.hi[fs * 4 + 2], pc.hi[fs * 4 + 3]};
-        const int sn[3] = {pc.nd[fs * 4 + 1], pc.nd[fs * 4 + 2], pc.nd[fs * 4 + 3]};
         u32 unused;
-        F::row_kara(xp, sl, sh, sn, pc.w[fs * 4], pc.c2p31, pc.c4, ylo, yhi);
-        F::bucket_sign_hl(ylo, yhi, mask, unused, sign);
+        F::row_sd(xp, pc.cl + 3 * fs, pc.ch + 3 * fs, pc.nd + 3 * fs, pc.k1[fs], pc.c2p31, pc.c4,
+                  ylo, yhi);
+        F::bucket_sign_sd(ylo, yhi, mask, unused, sign);
     }
 }
 
@@ -594,11 +610,29 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                     // until 128 keys (four a lane) are there to hash
                     const u32 qn = dd & 0x1FFu;
                     u32 missed = 0;
+                    bool miss[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        miss[q] = wt[q] != 0 && !dedup_count(tk, tc, dd_log2, (u64)key[q], wt[q]);
+                    if (a.glog2) {
+                        // the block's misses try the second-level table (the four
+                        // slot loads of a lane are in flight together)
+                        u32 gs[4];
+                        u64 gcur[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            gs[q] = gtable_slot((u64)key[q], a.glog2);
+                            gcur[q] = miss[q] ? __ldcg(a.gkeys + gs[q]) : DEDUP_EMPTY;
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (miss[q] && gtable_count(a.gkeys, a.gcounts, gs[q], (u64)key[q], gcur[q], wt[q]))
+                                miss[q] = false;
+                    }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const bool miss = wt[q] != 0 && !dedup_count(tk, tc, dd_log2, (u64)key[q], wt[q]);
-                        const u32 mb = __ballot_sync(0xffffffffu, miss);
-                        if (miss) {
+                        const u32 mb = __ballot_sync(0xffffffffu, miss[q]);
+                        if (miss[q]) {
                             const u32 pos = qn + missed + __popc(mb & lanes_below);
                             qk[pos] = (u64)key[q];
                             qc[pos] = wt[q];
@@ -808,6 +842,122 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
             const u32 b = (rank << lshift) + (i & (mloc - 1u));
             global_add64(a.counters + (((u64)row) << log2m) + b, (long long)v);
         }
+    }
+}
+
+// ------------------------------------------------------------ second-level table drain
+//
+// After an update that used the second-level key table: every key the table
+// holds is hashed once, with its count (Horner from the device copy of the
+// coefficients, the sketch's split), into the int64 counters -- exact by the
+// linearity of the Count Sketch (Sec. 1.3) -- and its slot is emptied for the
+// next update.  With the statistics hook on, each drained key counts as one
+// hashed entry.
+template <class F, int NF>
+__global__ void __launch_bounds__(256) k_gtable_drain(const UpdateArgs a) {
+    typedef FieldOps<F> Ops;
+    const u32 slots = 1u << a.glog2;
+    const u32 lane = threadIdx.x & 31u;
+    for (u32 i0 = blockIdx.x * blockDim.x; i0 < slots; i0 += gridDim.x * blockDim.x) {
+        const u32 i = i0 + threadIdx.x;
+        const u64 k = i < slots ? a.gkeys[i] : DEDUP_EMPTY;
+        const bool held = k != DEDUP_EMPTY;
+        if (a.hashed) {
+            const u32 b = __ballot_sync(0xffffffffu, held);
+            if (lane == 0 && b) atomicAdd(a.hashed, (unsigned long long)__popc(b));
+        }
+        if (!held) continue;
+        const int c = a.gcounts[i];
+        a.gkeys[i] = DEDUP_EMPTY;
+        a.gcounts[i] = 0;
+        const typename Ops::key_t key = (typename Ops::key_t)k;
+        update_big_key<F, NF>(Ops::prep(key), c, a.coef_dev, a.t, a.k, a.log2m, a.arb_r,
+                              a.counters);
+    }
+}
+
+// ------------------------------------------------------------ lean tile kernel
+//
+// The hot configuration on its own: p = 2^61-1, k = 4 (signed-digit power
+// sum, row_sd), compile-time t, one int32 counter tile per block in shared
+// memory (t * 2^log2m cells), two-for-one or two polynomials, int32 weights or
+// unit weights, log2m fixed at compile time (LOG2M > 0) or read at run time.
+// A thread takes four consecutive keys (and weights) per grid-stride step with
+// 16-byte loads, then hashes them one after the other, each row ending in one
+// shared atomic at tile + r * 4m + 4 * bucket; unaligned streams and the last
+// n mod 4 keys go one key at a time.  A key whose weight could overflow an
+// int32 tile counter (|w| > w_safe) goes to the int64 counters through the
+// cold Horner path.  The tile is added into the int64 counters at the end
+// (tile cell r * 2^log2m + b is counter r * 2^log2m + b).
+template <int T, int NF, bool WEIGHTED, int LOG2M, class PC>
+__device__ __forceinline__ void tile_key(const UpdateArgs& a, const PC& pc, u32 base, int log2m,
+                                         u64 key, int w) {
+    typedef msf::P61 F;
+    const u32 mask = (1u << log2m) - 1u;
+    const u32 row_bytes = 4u << log2m;
+    if (WEIGHTED && (u32)w + a.w_safe > 2u * a.w_safe) {  // |w| > w_safe (w_safe < 2^31)
+        update_big_key<F, NF>(FieldOps<F>::prep(key), w, a.coef_dev, T, 4, log2m, 0u, a.counters);
+        return;
+    }
+    F::Pow3 xp;
+    F::powers3(key, xp);
+#pragma unroll
+    for (int r = 0; r < T; ++r) {
+        u32 bucket, sb;
+        p61_row_bs<NF>(xp, pc, r, mask, 0u, bucket, sb);
+        const int d = sb ? -w : w;
+        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(base + (u32)r * row_bytes + (bucket << 2)),
+                     "r"(d)
+                     : "memory");
+    }
+}
+
+template <int T, int MODE, bool WEIGHTED, int LOG2M>
+__global__ void __launch_bounds__(512, 2)
+k_cs_update_tile(const UpdateArgs a,
+                 const ParamCoef<msf::P61, (MODE == CS_TWO_POLY ? 2 : 1) * T, 4> pc) {
+    constexpr int NF = (MODE == CS_TWO_POLY) ? 2 : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* tile = reinterpret_cast<int*>(smem);
+    const int log2m = LOG2M > 0 ? LOG2M : a.log2m;
+    const u32 cells = (u32)T << log2m;
+    for (u32 i = threadIdx.x; i < cells; i += blockDim.x) tile[i] = 0;
+    __syncthreads();
+    const u32 base = (u32)__cvta_generic_to_shared(tile);
+    const u64 n = a.n;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    const u64 first = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 groups = a.vec_ok ? n / 4 : 0;  // 16-byte aligned keys and weights
+    for (u64 g = first; g < groups; g += stride) {
+        const ulonglong2 k0 = __ldcs(reinterpret_cast<const ulonglong2*>(a.keys) + 2 * g);
+        const ulonglong2 k1 = __ldcs(reinterpret_cast<const ulonglong2*>(a.keys) + 2 * g + 1);
+        if (WEIGHTED) {
+            const int4 w4 = __ldcs(reinterpret_cast<const int4*>(a.weights) + g);
+            tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, k0.x, w4.x);
+            tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, k0.y, w4.y);
+            tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, k1.x, w4.z);
+            tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, k1.y, w4.w);
+        } else {
+            // unit weights: a rolled loop (the key registers rotate); unrolled,
+            // the compiler interleaves the four keys and runs out of registers
+            u64 kq[4] = {k0.x, k0.y, k1.x, k1.y};
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, kq[0], 1);
+                kq[0] = kq[1];
+                kq[1] = kq[2];
+                kq[2] = kq[3];
+            }
+        }
+    }
+    for (u64 j = groups * 4 + first; j < n; j += stride)
+        tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m,
+                                         __ldcs(reinterpret_cast<const u64*>(a.keys) + j),
+                                         WEIGHTED ? __ldcs(a.weights + j) : 1);
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < cells; i += blockDim.x) {
+        const int v = tile[i];
+        if (v != 0) global_add64(a.counters + i, (long long)v);
     }
 }
 

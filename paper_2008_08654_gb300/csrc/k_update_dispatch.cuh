@@ -17,18 +17,17 @@ static void fill_param_coef(ParamCoef<F, NFUN, K>& pc, const u64* words) {
     constexpr int W = FieldOps<F>::WORDS;
     pc.c2p31 = 0x80000000u;
     pc.c4 = 4u;
+    pc.cl[0] = pc.ch[0] = pc.nd[0] = 0;
+    pc.k1[0] = 0;
     if (NFUN == 0) {
         pc.w[0] = 0;
-        pc.lo[0] = pc.hi[0] = 0;
-        pc.nd[0] = 0;
         return;
     }
     for (int i = 0; i < NFUN * K * W; ++i) pc.w[i] = words[i];
-    for (int i = 0; i < NFUN * K; ++i) {
-        const u64 a = words[i * W];
-        pc.lo[i] = (u32)(a & 0x7FFFFFFFull);
-        pc.hi[i] = (u32)(a >> 31);
-        pc.nd[i] = (int)pc.lo[i] - (int)pc.hi[i];
+    if constexpr (ParamCoef<F, NFUN, K>::SD > 0) {
+        for (int f = 0; f < NFUN; ++f)
+            msf::P61::sd_coef(words + (size_t)f * K, pc.cl + 3 * f, pc.ch + 3 * f, pc.nd + 3 * f,
+                              pc.k1[f]);
     }
     if constexpr (K == 4 && PsLimbs<F>::N > 0) {
         for (int f = 0; f < NFUN; ++f) {
@@ -70,6 +69,22 @@ static cudaError_t launch_exact(const UpdateArgs& a, const u64* coef_host, const
                                 cudaStream_t stream, int* occupancy) {
     constexpr int NF = (MODE == CS_TWO_POLY) ? 2 : 1;
     auto kern = k_cs_update<F, T, K, MODE, PLACE, STRAT>;
+    // 2^61-1, k = 4, shared-memory tile, power-of-two buckets: the lean kernel
+    // (the statistics hook counts entries only in the general one)
+    if constexpr (std::is_same<F, msf::P61>::value && T > 0 && K == 4 && PLACE == PLACE_SMEM &&
+                  STRAT == STRAT_POWER_SUM) {
+        if (update_uses_lean_tile(PRIME_61, a, cfg.place, cfg.strategy)) {
+            // m = 2^10 and 2^12 (the workloads' widths) with compile-time row strides
+            if (a.weights)
+                kern = a.log2m == 10   ? k_cs_update_tile<T, MODE, true, 10>
+                       : a.log2m == 12 ? k_cs_update_tile<T, MODE, true, 12>
+                                       : k_cs_update_tile<T, MODE, true, 0>;
+            else
+                kern = a.log2m == 10   ? k_cs_update_tile<T, MODE, false, 10>
+                       : a.log2m == 12 ? k_cs_update_tile<T, MODE, false, 12>
+                                       : k_cs_update_tile<T, MODE, false, 0>;
+        }
+    }
     cudaError_t e;
     if (T == 0) {  // the generic kernel stages the coefficients after the tile
         const size_t tile = PLACE == PLACE_GLOBAL ? 0
@@ -158,12 +173,28 @@ cudaError_t launch_update_for(const UpdateArgs& a, const u64* coef_host, const L
                           : std::is_same<F, msf::P89>::value ? PRIME_89
                                                              : PRIME_64_59;
     if (update_is_specialized(PRIME, a.t, a.k, a.arb_r)) {
-        if (specialized) *specialized = 1;
+        if (specialized) *specialized = update_uses_lean_tile(PRIME, a, cfg.place, cfg.strategy) ? 2 : 1;
         return a.t == 5 ? launch_mode<F, 5, 4>(a, coef_host, cfg, stream, occupancy)
                         : launch_mode<F, 7, 4>(a, coef_host, cfg, stream, occupancy);
     }
     if (specialized) *specialized = 0;
     return launch_mode<F, 0, 0>(a, coef_host, cfg, stream, occupancy);
+}
+
+// The second-level table's drain (one-word keys only: 2^89-1 never uses it).
+template <class F>
+cudaError_t launch_gtable_drain_for(const UpdateArgs& a, cudaStream_t stream) {
+    if constexpr (!DedupKey<typename FieldOps<F>::key_t>::OK) {
+        return cudaErrorInvalidValue;
+    } else {
+        const u32 slots = 1u << a.glog2;
+        const unsigned blocks = (unsigned)((slots + 255u) / 256u < 4096u ? (slots + 255u) / 256u : 4096u);
+        if (a.mode == CS_TWO_POLY)
+            k_gtable_drain<F, 2><<<blocks, 256, 0, stream>>>(a);
+        else
+            k_gtable_drain<F, 1><<<blocks, 256, 0, stream>>>(a);
+        return cudaGetLastError();
+    }
 }
 
 }  // namespace msk

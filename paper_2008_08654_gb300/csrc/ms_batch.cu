@@ -186,12 +186,14 @@ extern "C" ms_status cs_batch_create(cs_batch** out, const cs_batch_job* jobs_ho
 }
 
 extern "C" ms_status cs_batch_launch(cs_batch* b, void* stream) {
+    msi::TraceRange trace_("cs_batch_launch");
     if (!b || !b->exec) return MS_ERR_INVALID_ARG;
     cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
     return e == cudaSuccess ? MS_OK : fail(e, "cs_batch_launch");
 }
 
 extern "C" ms_status cs_batch_launch_direct(cs_batch* b, void* stream) {
+    msi::TraceRange trace_("cs_batch_launch_direct");
     if (!b) return MS_ERR_INVALID_ARG;
     cudaError_t e = msk::launch_cs_update_batched(b->prime, b->args, b->launch, (cudaStream_t)stream,
                                                   nullptr);
@@ -217,6 +219,7 @@ extern "C" ms_status cs_batch_info(const cs_batch* b, uint64_t* total_keys, uint
 extern "C" ms_status cs_batch_tune(const cs_batch_job* jobs_host, int count,
                                    const cs_batch_tuning* candidates, int ncand, int reps,
                                    cs_batch_tuning* best, double* times_ms, void* stream) {
+    msi::TraceRange trace_("cs_batch_tune");
     if (!jobs_host || count < 1 || !candidates || ncand < 1 || reps < 1 || !best)
         return MS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -114,22 +114,53 @@ struct P61 {
         a = (u32)(hx >> 60);
     }
 
-    // ---- Karatsuba power sum (the update kernels' row hash) ----
+    // ---- power sum with signed digits (the update kernels' row hash) ----
     //
-    // Splits of x, x^2, x^3, each lazy (< 2^61 + 8): lo < 2^31, hi <= 2^30,
-    // d = hi - lo (a signed 32-bit value).
+    // A row is y = a0 + a1 x + a2 x^2 + a3 x^3 (mod p) with the powers X_i of x
+    // computed once per key, lazily reduced (X_i < 2^61 + 8).  Every operand
+    // of the row's products is split into two SIGNED 31-bit digits:
+    //   key side:  X - D = h 2^31 + l,  D = 2^60 + 2^30,
+    //              l = (X mod 2^31) - 2^30 in [-2^30, 2^30),
+    //              h = (X >> 31) - 2^29    in [-2^29, 2^29];
+    //   row side:  c = a_i or a_i - p, whichever is in (-2^60, 2^60),
+    //              c = ch 2^31 + cl,        cl in [-2^30, 2^30), ch in [-2^29, 2^29].
+    // The key-side offset D is a constant: a_i X = c (X - D) + c D, and
+    // sum_i c_i D joins a0 in the row constant K below.  With both digits that
+    // small, c (X - D) = ch h 2^62 + (ch l + cl h) 2^31 + cl l, and 2^62 = 2
+    // (mod p) gives, over the three terms,
+    //   H = sum ch h    (|H| <= 3 2^58),
+    //   A = sum cl l    (|A| <= 3 2^60),
+    //   M = sum (ch l + cl h) = A + H + sum (cl - ch)(h - l)   (Karatsuba;
+    //       |M| <= 3 2^60; |cl - ch|, |h - l| < 1.5 2^30 fit 32-bit operands),
+    //   row = A + 2H + 2^31 M + K   (mod p).
+    // Nine 32x32->64 multiply-adds in one chain give X1 = H, X2 = A + H and
+    // X3 = M as exact two's-complement 64-bit values; A + 2H = X1 + X2.
+    // With M = Mh 2^32 + Ml (Mh signed), 2^63 = 4 and 2^61 = 1 (mod p):
+    //   2^31 M = 4 Mh + (Ml >> 30) + (Ml mod 2^30) 2^31        (mod p)
+    //   S = A + 2H + (Ml mod 2^30) 2^31 + 4 Mh + (Ml >> 30)
+    //     in [-4.5 2^60 - 3 2^30, 6.5 2^60 + 2^32]
+    // and K = (a0 + D (a1 + a2 + a3)) mod p + 3p lies in [6 2^60 - 3, 8 2^60),
+    // so S + K is in [1.5 2^60 - 2^32, 14.5 2^60 + 2^32]: positive and far
+    // below 2^64 - 8, and the 64-bit sum needs no carry word.
+    // The row adds K + 1 (the "+1" of Algorithm div-simple, Sec. 1.5), so
+    // S1 = S + K + 1 = v + 1 for v = S + K, and Algorithm div-simple gives
+    //   z = floor(v / p) = ((S1 >> 61) + S1) >> 61,  v mod p = (v + z) & p,
+    // the canonical residue, branch free; (S1 >> 61) + S1 < 2^64 again.
     struct Pow3 {
-        u32 lo[3], hi[3];
-        int d[3];
+        int l[3], h[3], d[3];  // signed digits of X_i - D, and d = h - l
     };
 
-    __device__ static __forceinline__ void split3(u64 z, Pow3& xp, int i) {
-        xp.lo[i] = (u32)z & 0x7FFFFFFFu;
-        xp.hi[i] = (u32)(z >> 31);
-        xp.d[i] = (int)xp.hi[i] - (int)xp.lo[i];
+    // Signed digits of a lazy X < 2^61 + 8 (above).  X >> 31 <= 2^30.
+    __device__ static __forceinline__ void sdigits(u64 X, Pow3& xp, int i) {
+        const u32 lo = (u32)X, hi = (u32)(X >> 32);
+        const u32 lu = lo & 0x7FFFFFFFu;
+        const u32 hu = __funnelshift_r(lo, hi, 31);
+        xp.l[i] = (int)lu - (1 << 30);
+        xp.h[i] = (int)hu - (1 << 29);
+        xp.d[i] = (int)hu - (int)lu + ((1 << 30) - (1 << 29));  // h - l
     }
 
-    // x^2 for x = xh 2^31 + xl (lazy):
+    // x^2 for x = xh 2^31 + xl (lazy, unsigned digits):
     //   x^2 = xh^2 2^62 + xh xl 2^32 + xl^2 = 2 xh^2 + xl^2 + Q 2^32 with Q = xh xl
     //   Q 2^32 = (Q >> 29) 2^61 + (Q mod 2^29) 2^32 = (Q >> 29) + (Q mod 2^29) 2^32
     //   sum < 2^62 + 2^61 + 2^32 + 2^61 < 2^64; one fold gives < 2^61 + 4.
@@ -140,100 +171,88 @@ struct P61 {
         return fold(A + (Q >> 29) + ((Q & 0x1FFFFFFFull) << 32));
     }
 
-    // x = key mod p (lazy: (key & p) + (key >> 61) < 2^61 + 8), then x^2 and
-    // x^3 = x^2 * x, all three split.  The power-sum bounds below hold for lazy
-    // values, so no canonical reduction is needed here.
+    // x = key mod p (lazy: (key & p) + (key >> 61) < 2^61 + 8), x^2 and
+    // x^3 = x^2 * x (lazy), each in signed digits.
     __device__ static __forceinline__ void powers3(u64 key, Pow3& xp) {
         const u64 x1 = fold(key);
-        split3(x1, xp, 0);
-        const u64 x2 = square(xp.lo[0], xp.hi[0]);
-        split3(x2, xp, 1);
         Split s1;
-        s1.lo = xp.lo[0];
-        s1.hi = xp.hi[0];
-        s1.hi2 = xp.hi[0] << 1;
-        split3(mul_add(x2, s1, 0ull), xp, 2);
+        s1.lo = (u32)x1 & 0x7FFFFFFFu;
+        s1.hi = (u32)(x1 >> 31);
+        s1.hi2 = s1.hi << 1;
+        const u64 x2 = square(s1.lo, s1.hi);
+        const u64 x3 = mul_add(x2, s1, 0ull);
+        sdigits(x1, xp, 0);
+        sdigits(x2, xp, 1);
+        sdigits(x3, xp, 2);
     }
 
-    // One row: y = a0 + a1 x + a2 x^2 + a3 x^3 (mod p), lazy (< 2^61 + 8).
-    // With a_i = ah 2^31 + al and x^i = xh 2^31 + xl (2^62 = 2 mod p):
-    //   a_i x^i = al xl + 2 ah xh + (ah xl + al xh) 2^31
-    // and the cross terms by Karatsuba, three 32x32->64 products per term:
-    //   ah xl + al xh = al xl + ah xh + (al - ah)(xh - xl)
-    // Over the three terms (al < 2^31, ah < 2^30, xl < 2^31, xh <= 2^30):
-    //   A = sum al xl < 3 2^62,  H = sum ah xh < 3 2^60,
-    //   M = A + H + sum (al - ah)(xh - xl) = sum (ah xl + al xh) < 3 2^62
-    // (the signed products wrap modulo 2^64; M itself fits, so M is exact).
-    //   M 2^31 = 4 M.hi + (M.lo >> 30) + (M.lo mod 2^30) 2^31          (mod p)
-    //   A      = (A.hi mod 2^29 : A.lo) + (A.hi >> 29)                 (mod p)
-    //   S = (A.hi mod 2^29 : A.lo) + (M.lo mod 2^30) 2^31 + 4 M.hi + 2H
-    //       + (A.hi >> 29) + (M.lo >> 30) + a0
-    //     < 2^61 + 2^61 + 2^34 + 3 2^61 + 2^4 + 2^61 < 2^64
-    //   y = (S.hi mod 2^29 : S.lo) + (S.hi >> 29) < 2^61 + 8.
-    // c2p31 = 2^31 and c4 = 4 arrive as run-time operands so that both
-    // shift-adds stay wide multiply-adds.
-    __device__ static __forceinline__ void row_kara(const Pow3& xp, const u32* al, const u32* ah,
-                                                    const int* nd, u64 a0, u32 c2p31, u32 c4,
-                                                    u32& ylo, u32& yhi) {
-        asm("{\n\t"
-            ".reg .u64 A, H, E, M, T;\n\t"
-            ".reg .u32 Al, Ah, Ml, Mh, m0, m1, zA, zm, Tl, Th, z;\n\t"
-            "mul.wide.u32 A, %2, %11;\n\t"
-            "mad.wide.u32 A, %3, %14, A;\n\t"
-            "mad.wide.u32 A, %4, %17, A;\n\t"
-            "mul.wide.u32 H, %5, %12;\n\t"
-            "mad.wide.u32 H, %6, %15, H;\n\t"
-            "mad.wide.u32 H, %7, %18, H;\n\t"
-            "mul.wide.s32 E, %8, %13;\n\t"
-            "mad.wide.s32 E, %9, %16, E;\n\t"
-            "mad.wide.s32 E, %10, %19, E;\n\t"
-            "add.u64 M, A, H;\n\t"
-            "add.u64 M, M, E;\n\t"
-            "mov.b64 {Ml, Mh}, M;\n\t"
-            "and.b32 m0, Ml, 0x3FFFFFFF;\n\t"
-            "shr.u32 m1, Ml, 30;\n\t"
-            "mov.b64 {Al, Ah}, A;\n\t"
-            "shr.u32 zA, Ah, 29;\n\t"
-            "and.b32 Ah, Ah, 0x1FFFFFFF;\n\t"
-            "mov.b64 T, {Al, Ah};\n\t"
-            "mad.wide.u32 T, m0, %22, T;\n\t"
-            "mad.wide.u32 T, Mh, %23, T;\n\t"
-            "add.u64 T, T, H;\n\t"
-            "add.u64 T, T, H;\n\t"
-            "add.u32 zm, zA, m1;\n\t"
-            "mov.b64 {Tl, Th}, T;\n\t"
-            "add.cc.u32 Tl, Tl, zm;\n\t"
-            "addc.u32 Th, Th, 0;\n\t"
-            "add.cc.u32 Tl, Tl, %20;\n\t"
-            "addc.u32 Th, Th, %21;\n\t"
-            "shr.u32 z, Th, 29;\n\t"
-            "and.b32 Th, Th, 0x1FFFFFFF;\n\t"
-            "add.cc.u32 %0, Tl, z;\n\t"
-            "addc.u32 %1, Th, 0;\n\t"
-            "}"
-            : "=r"(ylo), "=r"(yhi)
-            : "r"(al[0]), "r"(al[1]), "r"(al[2]), "r"(ah[0]), "r"(ah[1]), "r"(ah[2]), "r"(nd[0]),
-              "r"(nd[1]), "r"(nd[2]), "r"(xp.lo[0]), "r"(xp.hi[0]), "r"(xp.d[0]), "r"(xp.lo[1]),
-              "r"(xp.hi[1]), "r"(xp.d[1]), "r"(xp.lo[2]), "r"(xp.hi[2]), "r"(xp.d[2]), "r"((u32)a0),
-              "r"((u32)(a0 >> 32)), "r"(c2p31), "r"(c4));
+    // One row (above): cl/ch/nd = the signed digits of a1..a3 and cl - ch,
+    // k1 = K + 1.  Returns the 64-bit word y64 = v + z with v mod p = y64 & p:
+    // the canonical residue is (yhi mod 2^29 : ylo), its bit 60 is bit 28 of
+    // yhi.  c2p31 = 2^31 and c4 = 4 arrive as run-time operands so that the
+    // two shifts of the fold stay wide multiply-adds.
+    __device__ static __forceinline__ void row_sd(const Pow3& xp, const int* cl, const int* ch,
+                                                  const int* nd, u64 k1, u32 c2p31, u32 c4,
+                                                  u32& ylo, u32& yhi) {
+        long long X1 = (long long)ch[0] * xp.h[0];
+        X1 += (long long)ch[1] * xp.h[1];
+        X1 += (long long)ch[2] * xp.h[2];                // H
+        long long X2 = X1 + (long long)cl[0] * xp.l[0];
+        X2 += (long long)cl[1] * xp.l[1];
+        X2 += (long long)cl[2] * xp.l[2];                // A + H
+        long long X3 = X2 + (long long)nd[0] * xp.d[0];
+        X3 += (long long)nd[1] * xp.d[1];
+        X3 += (long long)nd[2] * xp.d[2];                // M
+        const u32 Ml = (u32)X3;
+        const int Mh = (int)((u64)X3 >> 32);
+        u64 T = (u64)(Ml & 0x3FFFFFFFu) * c2p31 + (u64)X2;
+        T += (u64)((long long)Mh * (int)c4);
+        const u64 S1 = T + (u64)X1 + (Ml >> 30) + k1;   // S + K + 1 (no wrap)
+        const u32 z = (u32)((S1 + (S1 >> 61)) >> 61);   // floor(v / p)
+        const u64 y = S1 + z - 1;                        // v + z
+        ylo = (u32)y;
+        yhi = (u32)(y >> 32);
     }
 
-    // Bucket and sign bit of the canonical residue of a lazy y = (yhi:ylo)
-    // < 2^61 + 8, branch free.  y >= p exactly when y + 1 >= 2^61, i.e. when
-    // over = (y + 1) >> 61 = ((y + 1) >> 32) >> 29 is 1; then the residue is
-    // y - p = y + 1 - 2^61 < 9, whose low bits are those of ylo + 1 and whose
-    // bit 60 is 0.  Otherwise yhi < 2^29 and bit 60 is yhi >> 28.
-    // The canonical residue of a lazy y = (yhi:ylo) < 2^61 + 8 (same test as below).
-    __device__ static __forceinline__ u64 canon_hl(u32 ylo, u32 yhi) {
-        const u32 over = ((ylo == 0xFFFFFFFFu) ? yhi + 1u : yhi) >> 29;
-        return over ? (u64)(ylo + 1u) : (((u64)yhi << 32) | ylo);
+    // Row-side constants of row_sd for canonical a0..a3 < p (host or device):
+    // the signed digits of c_i = a_i or a_i - p (the one in (-2^60, 2^60)),
+    // cl_i - ch_i, and k1 = K + 1 with K = (a0 + D (a1 + a2 + a3)) mod p + 3p,
+    // D = 2^60 + 2^30.
+    __host__ __device__ static inline void sd_coef(const u64* a, int* cl, int* ch, int* nd,
+                                                   u64& k1) {
+        u64 s = 0;  // (a1 + a2 + a3) mod p
+        for (int i = 0; i < 3; ++i) {
+            const u64 ai = a[i + 1];
+            const long long c = ai <= (P >> 1) ? (long long)ai : (long long)ai - (long long)P;
+            const int l = ((int)((u32)(u64)c << 1)) >> 1;  // low 31 bits, sign-extended
+            cl[i] = l;
+            ch[i] = (int)((c - l) >> 31);                 // exact: c - l = 0 mod 2^31
+            nd[i] = cl[i] - ch[i];
+            s += ai;
+            if (s >= P) s -= P;
+        }
+        // 2^60 s = s / 2 (mod p), as 2^61 = 1: s / 2 for even s, (s + p) / 2 for odd s
+        const u64 s60 = (s & 1ull) ? (s + P) >> 1 : s >> 1;
+        // 2^30 s = (s mod 2^31) 2^30 + (s >> 31) 2^61 = (s mod 2^31) 2^30 + (s >> 31)
+        u64 s30 = ((s & 0x7FFFFFFFull) << 30) + (s >> 31);
+        if (s30 >= P) s30 -= P;
+        u64 k = a[0] + s60;
+        if (k >= P) k -= P;
+        k += s30;
+        if (k >= P) k -= P;
+        k1 = k + 3 * P + 1;
     }
 
-    __device__ static __forceinline__ void bucket_sign_hl(u32 ylo, u32 yhi, u32 mask, u32& bucket,
+    // The canonical residue from row_sd's output.
+    __device__ static __forceinline__ u64 canon_sd(u32 ylo, u32 yhi) {
+        return ((u64)(yhi & 0x1FFFFFFFu) << 32) | ylo;
+    }
+
+    // Bucket (low bits) and sign bit (bit 60) of the canonical residue.
+    __device__ static __forceinline__ void bucket_sign_sd(u32 ylo, u32 yhi, u32 mask, u32& bucket,
                                                           u32& sign) {
-        const u32 over = ((ylo == 0xFFFFFFFFu) ? yhi + 1u : yhi) >> 29;
-        bucket = (ylo + over) & mask;
-        sign = over ? 0u : (yhi >> 28);
+        bucket = ylo & mask;
+        sign = (yhi >> 28) & 1u;
     }
 };
 

@@ -1,7 +1,9 @@
 // Host side of the C ABI declared in include/ms.h: argument validation,
 // handle ownership, the coefficient draw, launch-configuration choice, and
 // error reporting.  Every computation is delegated to the kernels.
+#include <atomic>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -39,6 +41,11 @@ static const int kMaxReplicas = 32;   // replicas a large sketch owns (<= 64 MiB
 static const int kDefaultReplicas = 16;  // replicas a default launch uses
 static const int kDedupReplicas = 8;     // ... when the de-duplication table is on
 static const int kDedupLog2 = 12;        // de-duplication table: 4096 slots (48 KiB) per block
+// Second-level key table: 2^21 slots (24 MiB: keys and int32 counts, resident
+// in the L2 beside the replicas), used by de-duplicating updates of at least
+// 2^22 keys (aggregate 3 forces it, aggregate 2 turns it off).
+static const int kGTableLog2 = 21;
+static const uint64_t kGTableMinKeys = 1ull << 22;
 
 namespace {
 
@@ -205,6 +212,31 @@ extern "C" const char* ms_last_cuda_error(void) { return g_cuda_err; }
 
 extern "C" const char* ms_version(void) { return "1.0.0"; }
 
+// ---------------------------------------------------------------- tracing
+
+static std::atomic<int> g_tracing{-1};  // -1: not yet read from the environment
+
+bool msi::tracing() {
+    int v = g_tracing.load(std::memory_order_relaxed);
+    if (v < 0) {
+        const char* e = getenv("MS_NVTX");
+        v = (e && e[0] == '1') ? 1 : 0;
+        int expected = -1;
+        g_tracing.compare_exchange_strong(expected, v);
+        v = g_tracing.load(std::memory_order_relaxed);
+    }
+    return v == 1;
+}
+
+void msi::trace_push(const char* name) { nvtxRangePushA(name); }
+void msi::trace_pop() { nvtxRangePop(); }
+
+extern "C" int ms_set_tracing(int on) {
+    const int before = msi::tracing() ? 1 : 0;
+    g_tracing.store(on ? 1 : 0, std::memory_order_relaxed);
+    return before;
+}
+
 // ====================================================================== hashing
 
 struct ms_hash {
@@ -273,6 +305,7 @@ extern "C" ms_status ms_hash_params(const ms_hash* h, int* k, int* b, uint64_t* 
 
 extern "C" ms_status ms_hash_eval(const ms_hash* h, const void* keys_dev, void* out_dev, size_t n,
                                   void* stream) {
+    msi::TraceRange trace_("ms_hash_eval");
     if (!h) return MS_ERR_INVALID_ARG;
     if (n == 0) return MS_OK;
     if (!keys_dev || !out_dev) return MS_ERR_INVALID_ARG;
@@ -310,11 +343,13 @@ static ms_status divmod_common(int b, uint64_t c, const ms_u128* v, ms_u128* q, 
 
 extern "C" ms_status ms_div(int b, uint64_t c, const ms_u128* v_dev, ms_u128* q_dev, void* r_dev,
                             size_t n, void* stream) {
+    msi::TraceRange trace_("ms_div");
     return divmod_common(b, c, v_dev, q_dev, r_dev, n, stream);
 }
 
 extern "C" ms_status ms_mod(int b, uint64_t c, const ms_u128* v_dev, void* r_dev, size_t n,
                             void* stream) {
+    msi::TraceRange trace_("ms_mod");
     if (n > 0 && !r_dev) return MS_ERR_INVALID_ARG;
     return divmod_common(b, c, v_dev, nullptr, r_dev, n, stream);
 }
@@ -341,6 +376,31 @@ static void sketch_free_device(cs_sketch* sk) {
     sk->hcopy = nullptr;
     if (sk->hstage) cudaFree(sk->hstage);
     sk->hstage = nullptr;
+    if (sk->gtable) cudaFree(sk->gtable);
+    sk->gtable = nullptr;
+    sk->glog2 = 0;
+}
+
+// The second-level key table (allocated on first use, then kept): every key
+// slot free (all ones), every count zero.  The drain after each update leaves
+// it that way again.
+static ms_status ensure_gtable(cs_sketch* sk, int glog2) {
+    if (sk->gtable && sk->glog2 == glog2) return MS_OK;
+    if (sk->gtable) cudaFree(sk->gtable);
+    sk->gtable = nullptr;
+    sk->glog2 = 0;
+    const size_t slots = (size_t)1 << glog2;
+    ms_status st = msi::dev_alloc(&sk->gtable, slots * 12);
+    if (st != MS_OK) return st;
+    cudaError_t e = cudaMemset(sk->gtable, 0xFF, slots * 8);
+    if (e == cudaSuccess) e = cudaMemset((char*)sk->gtable + slots * 8, 0, slots * 4);
+    if (e != cudaSuccess) {
+        cudaFree(sk->gtable);
+        sk->gtable = nullptr;
+        return msi::cuda_fail(e, "second-level key table");
+    }
+    sk->glog2 = glog2;
+    return MS_OK;
 }
 
 static uint32_t next_pow2(uint32_t m) {
@@ -516,6 +576,13 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
 
     cfg.threads = ov.threads > 0 ? ov.threads : 256;
     cfg.strategy = ov.strategy >= 0 ? ov.strategy : msk::STRAT_POWER_SUM;
+    // strategy 2 (cs_set_launch): the power sum in the general kernel (four
+    // keys a thread) rather than the lean shared-memory-tile kernel
+    a.keys_per_thread_hint = 0;
+    if (cfg.strategy == 2) {
+        cfg.strategy = msk::STRAT_POWER_SUM;
+        a.keys_per_thread_hint = 4;
+    }
     cfg.cluster = 1;
     int place = ov.place;
     bool direct = false;  // PLACE_GLOBAL without replicas
@@ -549,7 +616,7 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
     // With the de-duplication table (unit weights, one-word keys) the hottest
     // keys reach the counters once per block, so fewer replicas suffice (8 vs
     // 16 measured 2% faster on the 2^28-key Zipf sketch, with half the reduce).
-    const int aggregate = ov.aggregate >= 0 ? ov.aggregate : 2;
+    const int aggregate = ov.aggregate >= 0 ? ov.aggregate : 3;
     const bool dedup_wanted = unit_weights && aggregate >= 2 && sk->prime != msk::PRIME_89;
     if (place == msk::PLACE_GLOBAL && !direct && sk->nrep > 0) {
         int r = ov.replicas > 0 ? ov.replicas : (dedup_wanted ? kDedupReplicas : kDefaultReplicas);
@@ -650,11 +717,32 @@ ms_status msi::choose_update_config(const cs_sketch* sk, uint64_t n, bool unit_w
     }
     // the table's int32 counts hold at most the keys one block sees
     if (a.dedup_log2 && iters * per_iter >= 0x7FFFFFFFull) set_dedup(false);
+    // the second-level key table (its int32 counts hold at most n); the
+    // caller points gkeys/gcounts at the sketch's table
+    a.glog2 = 0;
+    a.gkeys = nullptr;
+    a.gcounts = nullptr;
+    if (a.dedup_log2 && aggregate >= 3 && n < 0x7FFFFFFFull &&
+        (ov.aggregate == 3 || n >= kGTableMinKeys))
+        a.glog2 = kGTableLog2;
+    return MS_OK;
+}
+
+// Points an update's arguments at the sketch's second-level table (allocated
+// on first use) when the configuration asked for it.
+static ms_status attach_gtable(cs_sketch* sk, msk::UpdateArgs& a) {
+    if (!a.glog2) return MS_OK;
+    ms_status st = ensure_gtable(sk, a.glog2);
+    if (st != MS_OK) return st;
+    const size_t slots = (size_t)1 << a.glog2;
+    a.gkeys = (unsigned long long*)sk->gtable;
+    a.gcounts = (int*)((char*)sk->gtable + slots * 8);
     return MS_OK;
 }
 
 extern "C" ms_status cs_update(cs_sketch* sk, const void* keys_dev, const int32_t* weights_dev,
                                size_t n, void* stream) {
+    msi::TraceRange trace_("cs_update");
     if (!sk) return MS_ERR_INVALID_ARG;
     if (n == 0) return MS_OK;
     if (!keys_dev) return MS_ERR_INVALID_ARG;
@@ -669,9 +757,13 @@ extern "C" ms_status cs_update(cs_sketch* sk, const void* keys_dev, const int32_
     a.keys = keys_dev;
     a.weights = weights_dev;
     a.vec_ok = aligned(keys_dev, 16) && (!weights_dev || aligned(weights_dev, 16));
+    st = attach_gtable(sk, a);
+    if (st != MS_OK) return st;
     int spec = 0;
     MS_CUDA(msk::launch_cs_update(sk->prime, a, sk->words.data(), cfg, (cudaStream_t)stream, &spec),
             "cs_update");
+    if (a.glog2)
+        MS_CUDA(msk::launch_gtable_drain(sk->prime, a, (cudaStream_t)stream), "cs_update drain");
     if (a.replicas)
         MS_CUDA(msk::launch_reduce_replicas(sk->counters, sk->replicas, cfg.replicas,
                                             (u64)sk->t * sk->m, (cudaStream_t)stream),
@@ -685,6 +777,7 @@ static const uint64_t kHostChunk = 1ull << 24;  // keys per staging chunk of cs_
 
 extern "C" ms_status cs_update_host(cs_sketch* sk, const void* keys_host, const int32_t* weights_host,
                                     size_t n, void* stream) {
+    msi::TraceRange trace_("cs_update_host");
     if (!sk) return MS_ERR_INVALID_ARG;
     if (n == 0) return MS_OK;
     if (!keys_host) return MS_ERR_INVALID_ARG;
@@ -713,6 +806,8 @@ extern "C" ms_status cs_update_host(cs_sketch* sk, const void* keys_host, const 
     memset(&cfg, 0, sizeof(cfg));
     ms_status stt = choose_update_config(sk, n, weights_host == nullptr, a, cfg);
     if (stt != MS_OK) return stt;
+    stt = attach_gtable(sk, a);
+    if (stt != MS_OK) return stt;
     // the copies start after the work already on `stream` (which may still read
     // the staging chunks of an earlier call)
     MS_CUDA(cudaEventRecord(sk->hfree[0], st), "cs_update_host");
@@ -740,6 +835,7 @@ extern "C" ms_status cs_update_host(cs_sketch* sk, const void* keys_host, const 
         MS_CUDA(msk::launch_cs_update(sk->prime, a, sk->words.data(), cfg, st, &spec), "cs_update_host");
         MS_CUDA(cudaEventRecord(sk->hfree[buf], st), "cs_update_host");
     }
+    if (a.glog2) MS_CUDA(msk::launch_gtable_drain(sk->prime, a, st), "cs_update_host drain");
     if (a.replicas)
         MS_CUDA(msk::launch_reduce_replicas(sk->counters, sk->replicas, cfg.replicas,
                                             (u64)sk->t * sk->m, st),
@@ -751,6 +847,7 @@ extern "C" ms_status cs_update_host(cs_sketch* sk, const void* keys_host, const 
 
 extern "C" ms_status cs_estimate_f2(const cs_sketch* sk, ms_u128* out_dev, ms_u128* rows_dev,
                                     void* stream) {
+    msi::TraceRange trace_("cs_estimate_f2");
     if (!sk || !out_dev) return MS_ERR_INVALID_ARG;
     if (!aligned(out_dev, 16) || (rows_dev && !aligned(rows_dev, 16))) return MS_ERR_MISALIGNED;
     msk::F2Args a;
@@ -768,6 +865,7 @@ extern "C" ms_status cs_estimate_f2(const cs_sketch* sk, ms_u128* out_dev, ms_u1
 
 extern "C" ms_status cs_point_query(const cs_sketch* sk, const void* keys_dev, int64_t* out_dev,
                                     size_t n, void* stream) {
+    msi::TraceRange trace_("cs_point_query");
     if (!sk) return MS_ERR_INVALID_ARG;
     if (n == 0) return MS_OK;
     if (!keys_dev || !out_dev) return MS_ERR_INVALID_ARG;
@@ -794,12 +892,14 @@ extern "C" ms_status cs_counters(const cs_sketch* sk, int64_t** counters_dev) {
 }
 
 extern "C" ms_status cs_reset(cs_sketch* sk, void* stream) {
+    msi::TraceRange trace_("cs_reset");
     if (!sk) return MS_ERR_INVALID_ARG;
     MS_CUDA(msk::launch_zero(sk->counters, (u64)sk->t * sk->m * 8, (cudaStream_t)stream), "cs_reset");
     return MS_OK;
 }
 
 extern "C" ms_status cs_merge(cs_sketch* dst, const cs_sketch* src, void* stream) {
+    msi::TraceRange trace_("cs_merge");
     if (!dst || !src) return MS_ERR_INVALID_ARG;
     if (dst->t != src->t || dst->m != src->m || dst->r != src->r || dst->k != src->k ||
         dst->prime != src->prime || dst->mode != src->mode || dst->words != src->words)
@@ -828,6 +928,7 @@ const char kMagic[8] = {'M', 'S', 'C', 'S', 'K', 'E', 'T', '1'};
 }  // namespace
 
 extern "C" ms_status cs_export(const cs_sketch* sk, void* buf_host, size_t* size, void* stream) {
+    msi::TraceRange trace_("cs_export");
     if (!sk || !size) return MS_ERR_INVALID_ARG;
     const size_t need = sizeof(CkptHeader) + sk->words.size() * 8 + (size_t)sk->t * sk->m * 8;
     if (!buf_host) {
@@ -860,6 +961,7 @@ extern "C" ms_status cs_export(const cs_sketch* sk, void* buf_host, size_t* size
 }
 
 extern "C" ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size) {
+    msi::TraceRange trace_("cs_import");
     if (!out || !buf_host || size < sizeof(CkptHeader)) return MS_ERR_INVALID_ARG;
     *out = nullptr;
     CkptHeader h;
@@ -895,12 +997,12 @@ extern "C" ms_status cs_import(cs_sketch** out, const void* buf_host, size_t siz
 extern "C" ms_status cs_set_launch(cs_sketch* sk, int place, int strategy, int threads, int blocks,
                                    int blocks_per_sm, int cluster, int replicas, int aggregate) {
     if (!sk) return MS_ERR_INVALID_ARG;
-    if (place > 3 || strategy > msk::STRAT_POWER_SUM) return MS_ERR_INVALID_ARG;
+    if (place > 3 || strategy > 2) return MS_ERR_INVALID_ARG;  // 2: power sum, general kernel
     if (threads != 0 && threads != -1 &&
         (threads < 32 || threads > 512 || threads % 32 != 0))
         return MS_ERR_INVALID_ARG;
     if (cluster > 16 || (cluster > 0 && (cluster & (cluster - 1)) != 0)) return MS_ERR_INVALID_ARG;
-    if (replicas > 32 || (replicas > 0 && (replicas & (replicas - 1)) != 0) || aggregate > 2)
+    if (replicas > 32 || (replicas > 0 && (replicas & (replicas - 1)) != 0) || aggregate > 3)
         return MS_ERR_INVALID_ARG;
     sk->launch.place = place;
     sk->launch.strategy = strategy;
@@ -944,7 +1046,7 @@ extern "C" ms_status cs_last_launch(const cs_sketch* sk, int* place, int* strate
 
 extern "C" ms_status ms_probe_mul128(int variant, int iters, uint64_t* sink_dev, double* rate,
                                      double* ms) {
-    if (!sink_dev || !rate || !ms || iters < 1 || variant < 0 || variant > 3)
+    if (!sink_dev || !rate || !ms || iters < 1 || variant < 0 || variant > 4)
         return MS_ERR_INVALID_ARG;
     MS_CUDA(msk::run_probe_mul128(variant, iters, (u64*)sink_dev, rate, ms), "ms_probe_mul128");
     return MS_OK;

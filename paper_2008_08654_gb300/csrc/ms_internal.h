@@ -37,6 +37,10 @@ struct cs_sketch {
     int nrep = 0;                     // (large sketches only; zero between calls)
     // cs_update_host: two staging chunks, a copy stream and its events (lazy)
     void* hstage = nullptr;
+    // second-level key table of the de-duplicating update (lazy; empty
+    // between calls): 2^glog2 keys, then 2^glog2 int32 counts
+    void* gtable = nullptr;
+    int glog2 = 0;
     cudaStream_t hcopy = nullptr;
     cudaEvent_t hcopied[2] = {nullptr, nullptr};
     cudaEvent_t hfree[2] = {nullptr, nullptr};
@@ -47,6 +51,23 @@ struct cs_sketch {
 };
 
 namespace msi {
+// NVTX tracing (ms_set_tracing / MS_NVTX=1): off by default.  A range is
+// pushed only while tracing is on; the NVTX v3 calls are header-only and go
+// to a profiler's injection library when one is attached, else nowhere, so
+// the library links nothing extra.
+bool tracing();
+void trace_push(const char* name);
+void trace_pop();
+struct TraceRange {
+    bool on;
+    explicit TraceRange(const char* name) : on(tracing()) {
+        if (on) trace_push(name);
+    }
+    ~TraceRange() {
+        if (on) trace_pop();
+    }
+};
+
 ms_status cuda_fail(cudaError_t e, const char* where);
 int prime_id(int b, uint64_t c);
 int words_per_value(int prime);

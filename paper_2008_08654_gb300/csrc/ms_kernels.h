@@ -55,6 +55,14 @@ struct UpdateArgs {
     u32 arb_r;               // any number of buckets: r (rows are 2^log2m >= r wide);
                              // 0: power-of-two buckets (generic kernels only)
     unsigned long long* hashed;  // optional: += entries hashed with a non-zero count
+    int keys_per_thread_hint;    // 0: any kernel; 4: the general kernel (4 keys a thread)
+    // With the de-duplication table: the second-level key table in global
+    // memory (L2-resident), 2^glog2 slots of keys (DEDUP_EMPTY = free) and
+    // int32 counts; glog2 = 0: none.  Keys the block's table misses are
+    // counted there when they own (or claim) their slot.
+    unsigned long long* gkeys;
+    int* gcounts;
+    int glog2;
 };
 
 // Whether cs_update runs a compile-time (t, k) kernel (coefficients in the
@@ -64,6 +72,20 @@ struct UpdateArgs {
 inline bool update_is_specialized(int prime, int t, int k, u32 arb_r) {
     return k == 4 && (t == 5 || t == 7) && (arb_r == 0 || prime == PRIME_61);
 }
+
+// Whether a specialized 2^61-1 update with a shared-memory tile runs the lean
+// one-key-a-thread kernel (k_cs_update_tile) rather than the general one:
+// power-of-two buckets, no statistics hook, no request for the general kernel.
+inline bool update_uses_lean_tile(int prime, const UpdateArgs& a, int place, int strategy) {
+    return prime == PRIME_61 && a.k == 4 && (a.t == 5 || a.t == 7) && place == PLACE_SMEM &&
+           strategy == STRAT_POWER_SUM && a.arb_r == 0 && a.hashed == nullptr &&
+           a.keys_per_thread_hint == 0;
+}
+
+// Second-level key table: hashes every key it holds with its count into the
+// int64 counters (t rows, Horner from coef_dev, the split of the sketch's
+// mode) and empties the table for the next update.
+cudaError_t launch_gtable_drain(int prime, const UpdateArgs& a, cudaStream_t stream);
 
 // Launch configuration chosen on the host.
 struct LaunchCfg {
@@ -96,6 +118,10 @@ cudaError_t launch_update_p89(const UpdateArgs& a, const u64* coef_host, const L
                               cudaStream_t stream, int* specialized, int* occupancy);
 cudaError_t launch_update_p64(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
                               cudaStream_t stream, int* specialized, int* occupancy);
+cudaError_t launch_gtable_drain_p31(const UpdateArgs& a, cudaStream_t stream);
+cudaError_t launch_gtable_drain_p61(const UpdateArgs& a, cudaStream_t stream);
+cudaError_t launch_gtable_drain_p64(const UpdateArgs& a, cudaStream_t stream);
+cudaError_t launch_gtable_drain_p89(const UpdateArgs& a, cudaStream_t stream);
 
 struct F2Args {
     const long long* counters;

@@ -462,6 +462,7 @@ extern "C" ms_status ms_server_create(ms_server** out, const ms_server_config* c
 extern "C" ms_status ms_server_submit_update(ms_server* s, int sketch_id, const void* keys_host,
                                              const int32_t* weights_host, uint64_t n, int try_only,
                                              uint64_t* ticket) {
+    msi::TraceRange trace_("ms_server_submit_update");
     if (!s || sketch_id < 0 || sketch_id >= (int)s->sketches.size() || (n && !keys_host))
         return MS_ERR_INVALID_ARG;
     Req r;
@@ -482,6 +483,7 @@ extern "C" ms_status ms_server_submit_update(ms_server* s, int sketch_id, const 
 
 extern "C" ms_status ms_server_submit_query(ms_server* s, int sketch_id, int try_only,
                                             uint64_t* ticket) {
+    msi::TraceRange trace_("ms_server_submit_query");
     if (!s || sketch_id < 0 || sketch_id >= (int)s->sketches.size()) return MS_ERR_INVALID_ARG;
     Req r;
     r.kind = MS_REQ_QUERY;
@@ -503,6 +505,7 @@ extern "C" ms_status ms_server_poll(ms_server* s, uint64_t ticket, ms_request_re
 }
 
 extern "C" ms_status ms_server_drain(ms_server* s) {
+    msi::TraceRange trace_("ms_server_drain");
     if (!s) return MS_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lk(s->mu);
     const auto limit = std::chrono::duration<double>(s->cfg.timeout_s);
@@ -583,6 +586,7 @@ double percentile(std::vector<double>& v, double q) {
 }  // namespace
 
 extern "C" ms_status ms_server_run_load(ms_server* s, const ms_load_spec* sp, ms_load_result* out) {
+    msi::TraceRange trace_("ms_server_run_load");
     if (!s || !sp || !out || sp->count < 1 || sp->rate_per_s <= 0 || sp->min_keys < 1 ||
         sp->max_keys < sp->min_keys || !sp->key_pool_host || sp->pool_keys < sp->max_keys ||
         sp->query_fraction < 0 || sp->query_fraction > 1)

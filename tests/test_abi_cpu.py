@@ -156,5 +156,31 @@ def test_probes_and_stats_hook_validate_on_the_host(ms):
     assert lib.ms_probe_red(fake, 1 << 20, 4, None, ctypes.byref(t)) == 1
     assert lib.ms_probe_red(ctypes.c_void_p((1 << 20) + 2), 1 << 20, 4, ctypes.byref(r),
                             ctypes.byref(t)) == 8                                   # misaligned
-    assert lib.ms_probe_mul128(4, 16, fake, ctypes.byref(r), ctypes.byref(t)) == 1  # variant
+    assert lib.ms_probe_mul128(5, 16, fake, ctypes.byref(r), ctypes.byref(t)) == 1  # variant
     assert lib.cs_set_stats(None, None) == 1
+
+
+def test_tracing_is_off_by_default_and_needs_no_nvtx_library(ms):
+    """NVTX ranges are off unless asked for (MS_NVTX=1 or ms_set_tracing); the
+    library links no NVTX library (the header-only NVTX v3 calls reach a
+    profiler only when one injects itself), and with tracing on, entry points
+    still validate and return normally in a process without a GPU."""
+    import subprocess
+    import sys
+    out = subprocess.run(["readelf", "-d", ms.LIB_PATH], capture_output=True, text=True)
+    if out.returncode == 0:
+        needed = re.findall(r"\(NEEDED\)\s+Shared library: \[([^\]]+)\]", out.stdout)
+        assert needed and not any("nvToolsExt" in n or "nvtx" in n.lower() for n in needed), needed
+    code = ("import sys, ctypes; sys.path.insert(0, %r); import paper_2008_08654_gb300 as ms; "
+            "lib = ms.lib(); on = ms.set_tracing(True); "
+            "r = lib.cs_update(None, None, None, 10, None); "
+            "again = ms.set_tracing(False); print(int(on), int(again), r)") % ROOT
+    for env_val, first in (("", 0), ("1", 1)):
+        env = dict(os.environ)
+        env.pop("MS_NVTX", None)
+        if env_val:
+            env["MS_NVTX"] = env_val
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=300)
+        assert r.returncode == 0, r.stderr
+        assert r.stdout.split() == [str(first), "1", "1"], r.stdout

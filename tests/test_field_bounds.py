@@ -47,45 +47,102 @@ def h_ref(p, a, key):
     return sum(a[i] * pow(x, i, p) for i in range(len(a))) % p
 
 
-# ------------------------------------------------------------------ 2^61-1, Karatsuba rows
+# ------------------------------------------------------------------ 2^61-1, signed-digit rows
 
 P61 = (1 << 61) - 1
 
 
+def s64(v):
+    """A 64-bit word read as two's complement."""
+    v &= M64
+    return v - (1 << 64) if v >> 63 else v
+
+
+def sext31(w):
+    """The low 31 bits of a 32-bit word, sign-extended (the kernels' (int)(lo << 1) >> 1)."""
+    w &= 0x7FFFFFFF
+    return w - (1 << 31) if w >> 30 else w
+
+
+D61 = (1 << 60) + (1 << 30)  # the key-side digit offset of row_sd
+
+
+def p61_sdigits(X):
+    """sdigits: X - D = h 2^31 + l with l = (X mod 2^31) - 2^30 and h = (X >> 31) - 2^29."""
+    assert 0 <= X < (1 << 61) + 8
+    lo, hi = X & M32, X >> 32
+    lu = lo & 0x7FFFFFFF
+    hu = u32(((hi << 32) | lo) >> 31)
+    l, h = s32(lu - (1 << 30)), s32(hu - (1 << 29))
+    d = s32(hu - lu + (1 << 30) - (1 << 29))
+    assert X - D61 == h * (1 << 31) + l and d == h - l
+    assert -(1 << 30) <= l < (1 << 30) and -(1 << 29) <= h <= (1 << 29)
+    return l, h, d
+
+
+def p61_sd_coef(a):
+    """sd_coef: signed digits of c_i (a_i or a_i - p in (-2^60, 2^60)), cl - ch, k1."""
+    cl, ch, nd, s = [], [], [], 0
+    for ai in a[1:]:
+        c = ai if ai <= (P61 >> 1) else ai - P61
+        lo = sext31(c & M32)
+        assert (c - lo) % (1 << 31) == 0
+        hi = (c - lo) >> 31
+        assert -(1 << 30) <= lo < (1 << 30) and -(1 << 29) <= hi <= (1 << 29)
+        cl.append(lo)
+        ch.append(hi)
+        nd.append(s32(lo - hi))
+        s = (s + ai) % P61
+    s60 = (s + P61) >> 1 if s & 1 else s >> 1
+    assert (2 * s60) % P61 == s  # 2^60 s = s / 2 (mod p)
+    s30 = ((s & 0x7FFFFFFF) << 30) + (s >> 31)
+    s30 = s30 - P61 if s30 >= P61 else s30
+    assert s30 == (s << 30) % P61
+    k = (a[0] + s60) % P61
+    k = (k + s30) % P61
+    k1 = k + 3 * P61 + 1
+    assert k1 % P61 == (a[0] + D61 * sum(a[1:]) + 1) % P61
+    return cl, ch, nd, k1
+
+
 def p61_row(xs, a):
-    """row_kara on lazy powers xs (< 2^61 + 8) and canonical a[0..3]."""
-    al = [c & 0x7FFFFFFF for c in a[1:]]
-    ah = [c >> 31 for c in a[1:]]
-    nd = [al[i] - ah[i] for i in range(3)]
-    xl = [x & 0x7FFFFFFF for x in xs]
-    xh = [x >> 31 for x in xs]
-    assert all(v <= 1 << 30 for v in xh)
-    A = H = 0
-    E = 0
+    """row_sd on lazy powers xs (< 2^61 + 8) and canonical a[0..3]: returns the
+    64-bit word y64 whose low 61 bits are the canonical residue."""
+    cl, ch, nd, k1 = p61_sd_coef(a)
+    dg = [p61_sdigits(x) for x in xs]
+    X1 = 0
     for i in range(3):
-        A = madw(al[i], xl[i], A)
-        H = madw(ah[i], xh[i], H)
-        E = madws(nd[i], xh[i] - xl[i], E)
-    M = (A + H + E) & M64
-    assert M == sum(ah[i] * xl[i] + al[i] * xh[i] for i in range(3))
-    m0, m1 = (M & M32) & 0x3FFFFFFF, (M & M32) >> 30
-    zA = (A >> 32) >> 29
-    T = u64(((A >> 32) & 0x1FFFFFFF) << 32 | (A & M32))
-    T = madw(m0, 1 << 31, T)
-    T = madw(M >> 32, 4, T)
-    T = u64(T + 2 * H)
-    T = u64(T + zA + m1)
-    T = u64(T + a[0])
-    y = ((T >> 32) & 0x1FFFFFFF) << 32 | (T & M32)
-    y += (T >> 32) >> 29
-    assert y < (1 << 61) + 8
-    return y
+        X1 = madws(ch[i], dg[i][1], X1)
+    X2 = X1
+    for i in range(3):
+        X2 = madws(cl[i], dg[i][0], X2)
+    X3 = X2
+    for i in range(3):
+        X3 = madws(nd[i], dg[i][2], X3)
+    A = sum(cl[i] * dg[i][0] for i in range(3))
+    H = sum(ch[i] * dg[i][1] for i in range(3))
+    M = sum(cl[i] * dg[i][1] + ch[i] * dg[i][0] for i in range(3))
+    assert (s64(X1), s64(X2), s64(X3)) == (H, A + H, M)
+    assert abs(A) <= 3 << 60 and abs(H) <= 3 << 58 and abs(M) <= 3 << 60
+    Ml, Mh = X3 & M32, s64(X3) >> 32
+    m0, m1 = Ml & 0x3FFFFFFF, Ml >> 30
+    T = (u32(m0) * (1 << 31) + X2) & M64
+    T = madws(Mh, 4, T)
+    S1 = (T + X1 + m1 + k1) & M64
+    S = A + 2 * H + m0 * (1 << 31) + 4 * Mh + m1  # the value the words hold, without wrap
+    assert -(9 << 59) - (3 << 30) <= S <= (13 << 59) + (1 << 32)
+    assert S1 == S + k1 and 0 < S1 < M64 - 16  # no wrap: S1 = v + 1 exactly
+    q = S1 >> 61
+    W = u64(S1 + q)
+    z = W >> 61
+    assert z == (S1 - 1) // P61  # Algorithm div-simple: floor(v / p)
+    y64 = (S1 + z - 1) & M64
+    return y64
 
 
-def p61_bucket_sign(y, mask):
-    ylo, yhi = y & M32, y >> 32
-    over = ((yhi + 1) if ylo == M32 else yhi) >> 29
-    return (ylo + over) & mask, 0 if over else yhi >> 28
+def p61_bucket_sign(y64, mask):
+    """bucket_sign_sd: the low bits and bit 60 of the canonical residue."""
+    return (y64 & M32) & mask, ((y64 >> 32) >> 28) & 1
 
 
 def p61_powers(key):
@@ -265,9 +322,9 @@ def test_power_sum_rows_equal_the_definition(prime):
             if prime == 31:
                 b, s, y = p31_row(key, a, mask)
             elif prime == 61:
-                y = p61_row(p61_powers(key), a)
-                b, s = p61_bucket_sign(y, mask)
-                y = y - P61 if y >= P61 else y
+                y64 = p61_row(p61_powers(key), a)
+                b, s = p61_bucket_sign(y64, mask)
+                y = y64 & P61
             elif prime == 64:
                 b, s, y = p64_row(key, a, mask)
             else:
@@ -279,10 +336,17 @@ def test_power_sum_rows_equal_the_definition(prime):
 def test_rows_at_the_lazy_extremes():
     """The largest power limbs the lazy invariants allow, with the largest
     coefficients: every intermediate still fits its width."""
-    for a in ([P61 - 1] * 4, [P61 - 2, P61 - 1, (1 << 61) - (1 << 31), P61 - 1]):
-        for xs in ([(1 << 61) + 7] * 3, [1 << 61] * 3, [P61 - 1, (1 << 61) + 7, 0]):
-            y = p61_row(xs, a)
-            assert y % P61 == (a[0] + sum(a[i + 1] * xs[i] for i in range(3))) % P61
+    half = P61 >> 1
+    digit_edges = [0, 1, half, half + 1, half - (1 << 30), half + (1 << 30), P61 - 1,
+                   (1 << 30) - 1, 1 << 30, P61 - (1 << 30), (1 << 61) - (1 << 31)]
+    lazy = [0, (1 << 61) + 7, 1 << 61, P61 - 1, 1 << 60, (1 << 60) - 1, (1 << 60) + (1 << 30),
+            (1 << 60) - (1 << 30), (1 << 60) + (1 << 30) - 1, (1 << 61) - (1 << 30)]
+    for a in ([P61 - 1] * 4, [P61 - 2, P61 - 1, (1 << 61) - (1 << 31), P61 - 1]) + tuple(
+            [e, e, e, e] for e in digit_edges):
+        for xs in ([(1 << 61) + 7] * 3, [1 << 61] * 3, [P61 - 1, (1 << 61) + 7, 0]) + tuple(
+                [v, w, v] for v in lazy for w in lazy):
+            y = p61_row(xs, a) & P61
+            assert y == (a[0] + sum(a[i + 1] * xs[i] for i in range(3))) % P61
     top = [M30, M30, 1 << 29]
     for a in ([P89 - 1] * 4, [P89 - 2, P89 - 1, 1, P89 - 1], [M30] * 4, [0] * 4):
         for xl in ([top] * 3, [[0, 0, 0], top, [0, M30, 0]], [[M30, 0, 1 << 29]] * 3):
@@ -321,3 +385,33 @@ def test_p64_reduction_edges():
         key = rng.choice([0, P64 - 1, P64, (1 << 64) - 1, rng.randrange(1 << 64)])
         _, _, y = p64_row(key, a, 4095)
         assert y == h_ref(P64, a, key)
+
+
+def test_p61_rows_onto_p_and_at_digit_extremes():
+    """2^61-1: rows driven onto the residues p - 1, 0, 1, 2^60 - 1, 2^60, 2^60 + 1
+    (the canonical test of Algorithm div-simple and the sign bit), and operands
+    whose signed digits sit at their extremes (every 64-bit word of the row stays
+    within the bounds written beside row_sd)."""
+    rng = random.Random(61)
+    for target in (P61 - 1, P61 - 2, 0, 1, (1 << 60) - 1, 1 << 60, (1 << 60) + 1):
+        for _ in range(400):
+            key = rng.randrange(1 << 64)
+            a = [0] + [rng.randrange(P61) for _ in range(3)]
+            a[0] = (target - h_ref(P61, a, key)) % P61
+            y64 = p61_row(p61_powers(key), a)
+            assert y64 & P61 == target
+            assert p61_bucket_sign(y64, 1023) == (target & 1023, (target >> 60) & 1)
+    lo_e, hi_e = [-(1 << 30), (1 << 30) - 1, 0, 1], [-(1 << 29), 1 << 29, 0, -1]
+    for _ in range(4000):
+        a, xs = [rng.randrange(P61)], []
+        for _ in range(3):
+            c = rng.choice(hi_e) * (1 << 31) + rng.choice(lo_e)
+            while not -(1 << 60) < c < (1 << 60):
+                c = rng.choice(hi_e) * (1 << 31) + rng.choice(lo_e)
+            a.append(c % P61)
+            X = D61 + rng.choice(hi_e) * (1 << 31) + rng.choice(lo_e)
+            while not 0 <= X < (1 << 61) + 8:
+                X = D61 + rng.choice(hi_e) * (1 << 31) + rng.choice(lo_e)
+            xs.append(X)
+        y = p61_row(xs, a) & P61
+        assert y == (a[0] + sum(a[i + 1] * xs[i] for i in range(3))) % P61

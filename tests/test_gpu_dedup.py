@@ -75,7 +75,9 @@ def test_saturated_table_and_collisions(env):
     keys[rng.random(n) < 0.05] = np.uint64((1 << 64) - 1)
     keys[:64] = np.uint64((1 << 64) - 1)
     for blocks in (0, 1):
-        sketch_and_check(torch, ms, 61, 1, 5, 1 << 15, 4, 0, keys, 13, blocks=blocks)
+        for aggregate in (2, 3):
+            sketch_and_check(torch, ms, 61, 1, 5, 1 << 15, 4, 0, keys, 13, blocks=blocks,
+                             aggregate=aggregate)
 
 
 def test_all_equal_and_all_distinct(env):
@@ -101,28 +103,59 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("aggregate", [2, 3])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "-".join(map(str, c)))
-def test_modes_and_primes(env, case):
+def test_modes_and_primes(env, case, aggregate):
+    """aggregate 2: the block's table; 3: and the second-level table in global
+    memory (forced here on a short stream)."""
     torch, ms = env
     b, c, t, m, k, mode, strategy = case
     keys = zipf_keys(b, 150001, 40 + t + k)
-    sk, ll, want = sketch_and_check(torch, ms, b, c, t, m, k, mode, keys, 17 + t, strategy=strategy)
+    sk, ll, want = sketch_and_check(torch, ms, b, c, t, m, k, mode, keys, 17 + t, strategy=strategy,
+                                    aggregate=aggregate)
     assert sk.f2() == oracle.f2_estimate(want)
 
 
-def test_repeated_updates_accumulate(env):
-    """Two updates into one sketch: each launch drains its own tables."""
+@pytest.mark.parametrize("aggregate", [2, 3])
+def test_repeated_updates_accumulate(env, aggregate):
+    """Three updates into one sketch: each launch drains its own tables (the
+    second-level table is empty again after each)."""
     torch, ms = env
     keys = zipf_keys(61, 200003, 77)
     sk = ms.Sketch(t=7, m=1 << 16, k=4, seed=4)
-    sk.update(to_dev(torch, keys[:123457]))
-    sk.update(to_dev(torch, keys[123457:]))
+    sk.set_launch(aggregate=aggregate)
+    for lo, hi in ((0, 123457), (123457, 150001), (150001, 200003)):
+        sk.update(to_dev(torch, keys[lo:hi]))
     C = sk.counters().cpu().numpy()
     want = oracle.cs_update(61, 1, 4, 7, 1 << 16, 0, oracle.sketch_coeffs(61, 1, 4, 7, 0, 4), keys)
     assert np.array_equal(C, want)
 
 
-@pytest.mark.parametrize("aggregate", [0, 1, 2])
+def test_second_level_table_saturated(env):
+    """A default update of more than 2^22 keys (the second-level table on):
+    5 million distinct keys each seen about twice, so the 2^21-slot table
+    fills early and most of its lookups find another key; the table's EMPTY
+    word (all ones) repeated among them.  Also with the statistics hook: the
+    entries hashed stay below the keys."""
+    import os
+    torch, ms = env
+    n = (1 << 23) + 12345
+    rng = np.random.default_rng(11)
+    pool = datagen.u64_below(41, 0, 5_000_000)
+    keys = pool[rng.integers(0, pool.size, n)]
+    keys[rng.random(n) < 0.01] = np.uint64((1 << 64) - 1)
+    sk = ms.Sketch(t=7, m=1 << 16, k=4, seed=21)
+    hashed = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sk.set_stats(hashed)
+    sk.update(to_dev(torch, keys))
+    torch.cuda.synchronize()
+    want = oracle.cs_update(61, 1, 4, 7, 1 << 16, 0, oracle.sketch_coeffs(61, 1, 4, 7, 0, 21), keys,
+                            nthreads=os.cpu_count() or 1)
+    assert np.array_equal(sk.counters().cpu().numpy(), want)
+    assert 0 < int(hashed.item()) < n
+
+
+@pytest.mark.parametrize("aggregate", [0, 1, 2, 3])
 def test_aggregation_levels_agree(env, aggregate):
     """Off, warp merging, and the de-duplication table: one result."""
     torch, ms = env

@@ -157,7 +157,12 @@ CASES = [
     # b, c, t, m, k, mode, place, strategy, weights
     (61, 1, 5, 1024, 4, 0, -1, -1, "pm100"),    # config-1 shape, specialized, auto (smem)
     (61, 1, 5, 1024, 4, 0, 0, 0, "pm100"),      # Horner
-    (61, 1, 5, 1024, 4, 0, 0, 1, "unit"),       # power sum
+    (61, 1, 5, 1024, 4, 0, 0, 1, "unit"),       # power sum (lean tile kernel)
+    (61, 1, 5, 1024, 4, 0, 0, 2, "pm100"),      # power sum in the general kernel
+    (61, 1, 7, 4096, 4, 1, 0, 2, "unit"),       # two-poly, general kernel
+    (61, 1, 7, 4096, 4, 1, 0, 1, "pm100"),      # two-poly, lean kernel, 112 KiB tile
+    (61, 1, 5, 2, 4, 0, 0, 1, "pm100"),         # lean kernel, m = 2
+    (61, 1, 5, 4096, 4, 0, 0, 1, "unit"),       # lean kernel, unit weights, 80 KiB tile
     (61, 1, 5, 1024, 4, 1, 0, 1, "pm100"),      # two-poly, power sum
     (61, 1, 5, 1024, 4, 1, 0, 0, "pm100"),      # two-poly, Horner
     (61, 1, 7, 4096, 4, 0, -1, -1, "unit"),

@@ -1,6 +1,8 @@
 """The continuous-batching server: every query answer equals the oracle's F2
 estimate of its sketch over exactly the updates submitted to that sketch
 before the query -- whether requests run one at a time or mixed in batches."""
+import os
+
 import numpy as np
 import pytest
 
@@ -170,4 +172,53 @@ def test_server_page_locked_payloads_read_in_place():
     assert ans == want
     for i, c in enumerate(want_c):
         assert np.array_equal(srv.counters(i), c)
+    srv.close()
+
+
+def test_bounded_waits_time_out_on_the_host_and_the_server_recovers():
+    """Every blocking host wait of the server is bounded by timeout_s.  With one
+    slot and a 100-microsecond limit, a blocking submission behind a 2^24-key
+    update (its pageable copy alone takes milliseconds) and a drain while that
+    update is in flight both give up with MS_ERR_TIMEOUT -- no device wait is
+    involved.  The in-flight request still completes, and afterwards the server
+    answers exactly: counters and F2 equal the oracle over everything accepted."""
+    import time
+
+    import paper_2008_08654_gb300 as ms
+    widths, t, seed_base = [1024], 5, 313
+    srv = ms.Server(widths, t=t, seed_base=seed_base, staging_bytes=1 << 30, max_inflight=1,
+                    max_batch_keys=1 << 24, max_batch_requests=1, timeout_s=1e-4)
+    big = datagen.zipf(41, 1.1, 1 << 32, 1 << 24)
+    small = datagen.zipf(42, 1.1, 1 << 32, 1000)
+    t_big = srv.submit_update(0, big)
+    with pytest.raises(ms.MSError) as e:
+        srv.submit_update(0, small)  # blocks for a slot: the only one is taken
+    assert e.value.status == 6  # MS_ERR_TIMEOUT
+    with pytest.raises(ms.MSError) as e:
+        srv.drain()
+    assert e.value.status == 6
+    with pytest.raises(ms.MSError) as e:
+        srv.submit_query(0, try_only=True)  # the non-blocking form: busy
+    assert e.value.status == 7  # MS_ERR_BUSY
+
+    def wait_done(tk):
+        deadline = time.monotonic() + 60.0
+        while True:
+            r = srv.poll(tk)
+            if r["done"]:
+                return r
+            assert time.monotonic() < deadline, "request did not complete"
+            time.sleep(1e-3)
+
+    assert wait_done(t_big)["status"] == 0
+    t_small = srv.submit_update(0, small)
+    assert wait_done(t_small)["status"] == 0
+    r = wait_done(srv.submit_query(0))
+    C = np.zeros((t, widths[0]), dtype=np.int64)
+    coeffs = oracle.sketch_coeffs(61, 1, 4, t, 0, seed_base)
+    for keys in (big, small):
+        oracle.cs_update(61, 1, 4, t, widths[0], 0, coeffs, keys, None, counters=C,
+                         nthreads=os.cpu_count() or 1)
+    assert r["status"] == 0 and r["f2"] == oracle.f2_estimate(C)
+    assert np.array_equal(srv.counters(0), C)
     srv.close()
