@@ -117,12 +117,12 @@ __global__ void __launch_bounds__(1024) k_cs_update_batched(const BatchArgs a) {
                     auto row = [&](int r) {
                         const PsCoef cb = sps[(r - r0) * NF];
                         u32 ylo, yhi, bucket, sb;
-                        msf::P61::row_sd(xp, cb.cl, cb.ch, cb.nd, cb.k1, a.c2p31, a.c4, ylo, yhi);
+                        msf::P61::row_sd(xp, cb.cl, cb.ch, cb.nd, cb.k1, a.c2p31, ylo, yhi);
                         msf::P61::bucket_sign_sd(ylo, yhi, mask, bucket, sb);
                         if (MODE == CS_TWO_POLY) {
                             const PsCoef cs = sps[(r - r0) * NF + 1];
                             u32 unused;
-                            msf::P61::row_sd(xp, cs.cl, cs.ch, cs.nd, cs.k1, a.c2p31, a.c4, ylo, yhi);
+                            msf::P61::row_sd(xp, cs.cl, cs.ch, cs.nd, cs.k1, a.c2p31, ylo, yhi);
                             msf::P61::bucket_sign_sd(ylo, yhi, mask, unused, sb);
                         }
                         batched_add(tile, job.counters, r, r0, log2m, bucket, sb, wt[q], big[q]);

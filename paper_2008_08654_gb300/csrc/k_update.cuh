@@ -422,8 +422,7 @@ __device__ __forceinline__ void p61_row_bs(const msf::P61::Pow3& xp, const PC& p
     typedef msf::P61 F;
     const int fb = r * NF;
     u32 ylo, yhi;
-    F::row_sd(xp, pc.cl + 3 * fb, pc.ch + 3 * fb, pc.nd + 3 * fb, pc.k1[fb], pc.c2p31, pc.c4, ylo,
-              yhi);
+    F::row_sd(xp, pc.cl + 3 * fb, pc.ch + 3 * fb, pc.nd + 3 * fb, pc.k1[fb], pc.c2p31, ylo, yhi);
     if (ANY) {  // Algorithm Mersenne-arb-r on the canonical value
         u32 a;
         F::arb_split(F::canon_sd(ylo, yhi), arb_r, bucket, a);
@@ -434,8 +433,8 @@ __device__ __forceinline__ void p61_row_bs(const msf::P61::Pow3& xp, const PC& p
     if (NF == 2) {
         const int fs = fb + 1;
         u32 unused;
-        F::row_sd(xp, pc.cl + 3 * fs, pc.ch + 3 * fs, pc.nd + 3 * fs, pc.k1[fs], pc.c2p31, pc.c4,
-                  ylo, yhi);
+        F::row_sd(xp, pc.cl + 3 * fs, pc.ch + 3 * fs, pc.nd + 3 * fs, pc.k1[fs], pc.c2p31, ylo,
+                  yhi);
         F::bucket_sign_sd(ylo, yhi, mask, unused, sign);
     }
 }
@@ -882,78 +881,93 @@ __global__ void __launch_bounds__(256) k_gtable_drain(const UpdateArgs a) {
 // sum, row_sd), compile-time t, one int32 counter tile per block in shared
 // memory (t * 2^log2m cells), two-for-one or two polynomials, int32 weights or
 // unit weights, log2m fixed at compile time (LOG2M > 0) or read at run time.
-// A thread takes four consecutive keys (and weights) per grid-stride step with
-// 16-byte loads, then hashes them one after the other, each row ending in one
-// shared atomic at tile + r * 4m + 4 * bucket; unaligned streams and the last
-// n mod 4 keys go one key at a time.  A key whose weight could overflow an
-// int32 tile counter (|w| > w_safe) goes to the int64 counters through the
-// cold Horner path.  The tile is added into the int64 counters at the end
-// (tile cell r * 2^log2m + b is counter r * 2^log2m + b).
-template <int T, int NF, bool WEIGHTED, int LOG2M, class PC>
-__device__ __forceinline__ void tile_key(const UpdateArgs& a, const PC& pc, u32 base, int log2m,
-                                         u64 key, int w) {
-    typedef msf::P61 F;
-    const u32 mask = (1u << log2m) - 1u;
-    const u32 row_bytes = 4u << log2m;
-    if (WEIGHTED && (u32)w + a.w_safe > 2u * a.w_safe) {  // |w| > w_safe (w_safe < 2^31)
-        update_big_key<F, NF>(FieldOps<F>::prep(key), w, a.coef_dev, T, 4, log2m, 0u, a.counters);
-        return;
-    }
-    F::Pow3 xp;
-    F::powers3(key, xp);
-#pragma unroll
-    for (int r = 0; r < T; ++r) {
-        u32 bucket, sb;
-        p61_row_bs<NF>(xp, pc, r, mask, 0u, bucket, sb);
-        const int d = sb ? -w : w;
-        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(base + (u32)r * row_bytes + (bucket << 2)),
-                     "r"(d)
-                     : "memory");
-    }
-}
-
+// A thread takes four consecutive keys (and weights) per grid-stride step --
+// 16-byte loads when the stream is aligned and the group is whole, else
+// element loads with weight 0 past the end -- and hashes them one after the
+// other, each row ending in one shared atomic at tile + r * 4m + 4 * bucket.
+// A key whose weight could overflow an int32 tile counter (|w| > w_safe) goes
+// to the int64 counters through the cold Horner path.  The tile is added into
+// the int64 counters at the end (tile cell r * 2^log2m + b is counter
+// r * 2^log2m + b).  The t = 5 two-for-one kernels are capped at 42 registers
+// (three 512-thread blocks per SM), the others at 64.  With unit weights the
+// four keys go through a rolled loop (their registers rotate): unrolled, the
+// compiler interleaves them and spills.
 template <int T, int MODE, bool WEIGHTED, int LOG2M>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(512, (MODE != CS_TWO_POLY && T == 5) ? 3 : 2)
 k_cs_update_tile(const UpdateArgs a,
                  const ParamCoef<msf::P61, (MODE == CS_TWO_POLY ? 2 : 1) * T, 4> pc) {
+    typedef msf::P61 F;
     constexpr int NF = (MODE == CS_TWO_POLY) ? 2 : 1;
     extern __shared__ __align__(16) unsigned char smem[];
     int* tile = reinterpret_cast<int*>(smem);
     const int log2m = LOG2M > 0 ? LOG2M : a.log2m;
+    const u32 mask = (1u << log2m) - 1u;
+    const u32 row_bytes = 4u << log2m;
     const u32 cells = (u32)T << log2m;
     for (u32 i = threadIdx.x; i < cells; i += blockDim.x) tile[i] = 0;
     __syncthreads();
     const u32 base = (u32)__cvta_generic_to_shared(tile);
     const u64 n = a.n;
+    const u32 w_safe = a.w_safe;
+    const bool vec = a.vec_ok != 0;
+    const u64* keys = reinterpret_cast<const u64*>(a.keys);
+    const u64 groups = (n + 3) / 4;
     const u64 stride = (u64)gridDim.x * blockDim.x;
-    const u64 first = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    const u64 groups = a.vec_ok ? n / 4 : 0;  // 16-byte aligned keys and weights
-    for (u64 g = first; g < groups; g += stride) {
-        const ulonglong2 k0 = __ldcs(reinterpret_cast<const ulonglong2*>(a.keys) + 2 * g);
-        const ulonglong2 k1 = __ldcs(reinterpret_cast<const ulonglong2*>(a.keys) + 2 * g + 1);
-        if (WEIGHTED) {
-            const int4 w4 = __ldcs(reinterpret_cast<const int4*>(a.weights) + g);
-            tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, k0.x, w4.x);
-            tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, k0.y, w4.y);
-            tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, k1.x, w4.z);
-            tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, k1.y, w4.w);
+    for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += stride) {
+        const u64 j = 4 * g;
+        u64 key[4];
+        int wt[4];
+        if (vec && j + 3 < n) {
+            const ulonglong2 k0 = __ldcs(reinterpret_cast<const ulonglong2*>(keys + j));
+            const ulonglong2 k1 = __ldcs(reinterpret_cast<const ulonglong2*>(keys + j) + 1);
+            key[0] = k0.x; key[1] = k0.y; key[2] = k1.x; key[3] = k1.y;
+            if (WEIGHTED) {
+                const int4 w4 = __ldcs(reinterpret_cast<const int4*>(a.weights + j));
+                wt[0] = w4.x; wt[1] = w4.y; wt[2] = w4.z; wt[3] = w4.w;
+            } else {
+                wt[0] = wt[1] = wt[2] = wt[3] = 1;
+            }
         } else {
-            // unit weights: a rolled loop (the key registers rotate); unrolled,
-            // the compiler interleaves the four keys and runs out of registers
-            u64 kq[4] = {k0.x, k0.y, k1.x, k1.y};
-#pragma unroll 1
-            for (int q = 0; q < 4; ++q) {
-                tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m, kq[0], 1);
-                kq[0] = kq[1];
-                kq[1] = kq[2];
-                kq[2] = kq[3];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {  // past the end: key 0 with weight 0 (adds nothing)
+                const bool in = j + q < n;
+                key[q] = in ? __ldcs(keys + j + q) : 0ull;
+                wt[q] = in ? (WEIGHTED ? __ldcs(a.weights + j + q) : 1) : 0;
+            }
+        }
+#pragma unroll(WEIGHTED ? 4 : 1)
+        for (int q = 0; q < 4; ++q) {
+            const u64 kq = key[0];
+            const int w = wt[0];
+            key[0] = key[1];
+            key[1] = key[2];
+            key[2] = key[3];
+            wt[0] = wt[1];
+            wt[1] = wt[2];
+            wt[2] = wt[3];
+            if (WEIGHTED && (u32)w + w_safe > 2u * w_safe) {  // |w| > w_safe (w_safe < 2^31)
+                update_big_key<F, NF>(FieldOps<F>::prep(kq), w, a.coef_dev, T, 4, log2m, 0u,
+                                      a.counters);
+                continue;
+            }
+            F::Pow3 xp;
+            F::powers3(kq, xp);
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                u32 ylo, yhi;
+                F::row_sd(xp, pc.cl + 3 * NF * r, pc.ch + 3 * NF * r, pc.nd + 3 * NF * r,
+                          pc.k1[NF * r], pc.c2p31, ylo, yhi);
+                const u32 bucket = ylo & mask;
+                if (NF == 2)  // the sign from the second polynomial's bit 60
+                    F::row_sd(xp, pc.cl + 3 * (2 * r + 1), pc.ch + 3 * (2 * r + 1),
+                              pc.nd + 3 * (2 * r + 1), pc.k1[2 * r + 1], pc.c2p31, ylo, yhi);
+                const int d = (yhi & 0x10000000u) ? -w : w;  // bit 60 of the residue
+                asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(base + (u32)r * row_bytes + (bucket << 2)),
+                             "r"(d)
+                             : "memory");
             }
         }
     }
-    for (u64 j = groups * 4 + first; j < n; j += stride)
-        tile_key<T, NF, WEIGHTED, LOG2M>(a, pc, base, log2m,
-                                         __ldcs(reinterpret_cast<const u64*>(a.keys) + j),
-                                         WEIGHTED ? __ldcs(a.weights + j) : 1);
     __syncthreads();
     for (u32 i = threadIdx.x; i < cells; i += blockDim.x) {
         const int v = tile[i];

@@ -135,10 +135,10 @@ struct P61 {
     //   row = A + 2H + 2^31 M + K   (mod p).
     // Nine 32x32->64 multiply-adds in one chain give X1 = H, X2 = A + H and
     // X3 = M as exact two's-complement 64-bit values; A + 2H = X1 + X2.
-    // With M = Mh 2^32 + Ml (Mh signed), 2^63 = 4 and 2^61 = 1 (mod p):
-    //   2^31 M = 4 Mh + (Ml >> 30) + (Ml mod 2^30) 2^31        (mod p)
-    //   S = A + 2H + (Ml mod 2^30) 2^31 + 4 Mh + (Ml >> 30)
-    //     in [-4.5 2^60 - 3 2^30, 6.5 2^60 + 2^32]
+    // With M = M1 2^30 + m0 (m0 = M mod 2^30, M1 = M >> 30 arithmetic,
+    // |M1| <= 3 2^30) and 2^61 = 1 (mod p):
+    //   2^31 M = M1 2^61 + m0 2^31 = M1 + m0 2^31                 (mod p)
+    //   S = A + 2H + m0 2^31 + M1  in [-4.5 2^60 - 3 2^30, 6.5 2^60 + 3 2^30]
     // and K = (a0 + D (a1 + a2 + a3)) mod p + 3p lies in [6 2^60 - 3, 8 2^60),
     // so S + K is in [1.5 2^60 - 2^32, 14.5 2^60 + 2^32]: positive and far
     // below 2^64 - 8, and the 64-bit sum needs no carry word.
@@ -189,11 +189,11 @@ struct P61 {
     // One row (above): cl/ch/nd = the signed digits of a1..a3 and cl - ch,
     // k1 = K + 1.  Returns the 64-bit word y64 = v + z with v mod p = y64 & p:
     // the canonical residue is (yhi mod 2^29 : ylo), its bit 60 is bit 28 of
-    // yhi.  c2p31 = 2^31 and c4 = 4 arrive as run-time operands so that the
-    // two shifts of the fold stay wide multiply-adds.
+    // yhi.  c2p31 = 2^31 arrives as a run-time operand so that m0 2^31 + X2
+    // stays one wide multiply-add.
     __device__ static __forceinline__ void row_sd(const Pow3& xp, const int* cl, const int* ch,
-                                                  const int* nd, u64 k1, u32 c2p31, u32 c4,
-                                                  u32& ylo, u32& yhi) {
+                                                  const int* nd, u64 k1, u32 c2p31, u32& ylo,
+                                                  u32& yhi) {
         long long X1 = (long long)ch[0] * xp.h[0];
         X1 += (long long)ch[1] * xp.h[1];
         X1 += (long long)ch[2] * xp.h[2];                // H
@@ -203,11 +203,10 @@ struct P61 {
         long long X3 = X2 + (long long)nd[0] * xp.d[0];
         X3 += (long long)nd[1] * xp.d[1];
         X3 += (long long)nd[2] * xp.d[2];                // M
-        const u32 Ml = (u32)X3;
-        const int Mh = (int)((u64)X3 >> 32);
-        u64 T = (u64)(Ml & 0x3FFFFFFFu) * c2p31 + (u64)X2;
-        T += (u64)((long long)Mh * (int)c4);
-        const u64 S1 = T + (u64)X1 + (Ml >> 30) + k1;   // S + K + 1 (no wrap)
+        const u32 m0 = (u32)X3 & 0x3FFFFFFFu;
+        const long long M1 = X3 >> 30;
+        const u64 T = (u64)m0 * c2p31 + (u64)X2;
+        const u64 S1 = T + (u64)X1 + (u64)M1 + k1;      // S + K + 1 (no wrap)
         const u32 z = (u32)((S1 + (S1 >> 61)) >> 61);   // floor(v / p)
         const u64 y = S1 + z - 1;                        // v + z
         ylo = (u32)y;

@@ -124,13 +124,12 @@ def p61_row(xs, a):
     M = sum(cl[i] * dg[i][1] + ch[i] * dg[i][0] for i in range(3))
     assert (s64(X1), s64(X2), s64(X3)) == (H, A + H, M)
     assert abs(A) <= 3 << 60 and abs(H) <= 3 << 58 and abs(M) <= 3 << 60
-    Ml, Mh = X3 & M32, s64(X3) >> 32
-    m0, m1 = Ml & 0x3FFFFFFF, Ml >> 30
+    m0, M1 = X3 & 0x3FFFFFFF, s64(X3) >> 30
+    assert abs(M1) <= 3 << 30 and M == M1 * (1 << 30) + m0
     T = (u32(m0) * (1 << 31) + X2) & M64
-    T = madws(Mh, 4, T)
-    S1 = (T + X1 + m1 + k1) & M64
-    S = A + 2 * H + m0 * (1 << 31) + 4 * Mh + m1  # the value the words hold, without wrap
-    assert -(9 << 59) - (3 << 30) <= S <= (13 << 59) + (1 << 32)
+    S1 = (T + X1 + M1 + k1) & M64
+    S = A + 2 * H + m0 * (1 << 31) + M1  # the value the words hold, without wrap
+    assert -(9 << 59) - (3 << 30) <= S <= (13 << 59) + (3 << 30)
     assert S1 == S + k1 and 0 < S1 < M64 - 16  # no wrap: S1 = v + 1 exactly
     q = S1 >> 61
     W = u64(S1 + q)
