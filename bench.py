@@ -65,8 +65,8 @@ WORKLOADS = {
 # configuration; the stream's traffic grows in proportion, so a launch's traffic
 # is this times its keys.  Only workloads whose current kernel was captured.
 MEASURED_TRAFFIC_PER_KEY = {
-    "large": (283.502336e6 + 3.677952e6) / 2 ** 25,
-    "plain-2^28": (402.738688e6 + 3.371264e6) / 2 ** 25,
+    "large": (308.845056e6 + 8.336896e6) / 2 ** 25,
+    "plain-2^28": (402.739200e6 + 3.022336e6) / 2 ** 25,
 }
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
