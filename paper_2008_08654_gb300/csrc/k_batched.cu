@@ -109,23 +109,31 @@ __global__ void __launch_bounds__(1024) k_cs_update_batched(const BatchArgs a) {
             if constexpr (PS) {
                 // one key at a time (its powers, then the item's rows): few live
                 // registers, so up to 1024 threads per block
+                const u32 tbase = (u32)__cvta_generic_to_shared(tile);
+                const u32 row_bytes = 4u << log2m;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    if (wt[q] == 0) continue;  // ragged end of the chunk
+                    const int w = wt[q];
+                    if (w == 0) continue;  // ragged end of the chunk
+                    const bool bq = big[q];
                     msf::P61::Pow3 xp;
                     msf::P61::powers3(key[q], xp);
                     auto row = [&](int r) {
                         const PsCoef cb = sps[(r - r0) * NF];
-                        u32 ylo, yhi, bucket, sb;
+                        u32 ylo, yhi;
                         msf::P61::row_sd(xp, cb.cl, cb.ch, cb.nd, cb.k1, a.c2p31, ylo, yhi);
-                        msf::P61::bucket_sign_sd(ylo, yhi, mask, bucket, sb);
+                        const u32 bucket = ylo & mask;
                         if (MODE == CS_TWO_POLY) {
                             const PsCoef cs = sps[(r - r0) * NF + 1];
-                            u32 unused;
                             msf::P61::row_sd(xp, cs.cl, cs.ch, cs.nd, cs.k1, a.c2p31, ylo, yhi);
-                            msf::P61::bucket_sign_sd(ylo, yhi, mask, unused, sb);
                         }
-                        batched_add(tile, job.counters, r, r0, log2m, bucket, sb, wt[q], big[q]);
+                        const int d = (yhi & 0x10000000u) ? -w : w;  // bit 60 of the residue
+                        if (bq)
+                            global_add64(job.counters + (((u64)r) << log2m) + bucket, (long long)d);
+                        else
+                            asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(tbase + (u32)(r - r0) * row_bytes + (bucket << 2)),
+                                         "r"(d)
+                                         : "memory");
                     };
                     if (r1 - r0 == 5) {
                         // five rows (every item of a t = 5 sketch): unrolled, so
