@@ -173,9 +173,10 @@ class ClockSampler:
 def mad_wide_per_entry(t: int, nf: int) -> int:
     """32x32->64 multiply-adds (mad.wide) one hashed entry costs in the 2^61-1,
     k = 4 update kernels, counted from the row code (ms_field.cuh, row_sd and
-    powers3): per row 9 products (Karatsuba on signed 31-bit digits) and 2
-    fold steps (2^31 and 4 as wide multiply-adds); per key x^2 (3) and x^3 (4)."""
-    return 11 * t * nf + 7
+    powers3): per row 9 products (Karatsuba on signed 31-bit digits) and 1
+    fold step (the low 30 bits of the last sum times 2^31, a wide
+    multiply-add); per key x^2 (3) and x^3 (4)."""
+    return 10 * t * nf + 7
 
 
 def hbm_peak_gbs() -> tuple:
