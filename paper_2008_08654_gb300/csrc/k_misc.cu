@@ -167,12 +167,13 @@ cudaError_t launch_cs_update(int prime, const UpdateArgs& a, const u64* coef_hos
     }
 }
 
-cudaError_t launch_gtable_drain(int prime, const UpdateArgs& a, cudaStream_t stream) {
+cudaError_t launch_gtable_drain(int prime, const UpdateArgs& a, const u64* coef_host,
+                                cudaStream_t stream) {
     switch (prime) {
-        case PRIME_31: return launch_gtable_drain_p31(a, stream);
-        case PRIME_61: return launch_gtable_drain_p61(a, stream);
-        case PRIME_89: return launch_gtable_drain_p89(a, stream);
-        default: return launch_gtable_drain_p64(a, stream);
+        case PRIME_31: return launch_gtable_drain_p31(a, coef_host, stream);
+        case PRIME_61: return launch_gtable_drain_p61(a, coef_host, stream);
+        case PRIME_89: return launch_gtable_drain_p89(a, coef_host, stream);
+        default: return launch_gtable_drain_p64(a, coef_host, stream);
     }
 }
 

@@ -710,19 +710,31 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                 }
             }
             if constexpr (PLACE == PLACE_GLOBAL) {
-                // rows outer: the four keys' atomics of a row go out together
-                msf::P61::Pow3 xp[4];
+                // two keys' powers live at a time (a rolled loop over the two
+                // pairs, whose registers rotate; rows outer within a pair): with
+                // all four keys' powers live the de-duplicating path spilled
+                // under the 64-register cap
+#pragma unroll 1
+                for (int qq = 0; qq < 2; ++qq) {
+                    msf::P61::Pow3 xp[2];
+                    msf::P61::powers3(key[0], xp[0]);
+                    msf::P61::powers3(key[1], xp[1]);
+                    const int w0 = wt[0], w1 = wt[1];
+                    key[0] = key[2];
+                    key[1] = key[3];
+                    wt[0] = wt[2];
+                    wt[1] = wt[3];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) msf::P61::powers3(key[q], xp[q]);
-#pragma unroll
-                for (int r = 0; r < T; ++r) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int r = 0; r < T; ++r) {
                         u32 bucket, sb;
-                        p61_row_bs<NF, STRAT == STRAT_POWER_SUM_ANY_R>(xp[q], pc, r, mask, a.arb_r,
+                        p61_row_bs<NF, STRAT == STRAT_POWER_SUM_ANY_R>(xp[0], pc, r, mask, a.arb_r,
                                                                        bucket, sb);
-                        apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket,
-                                          sb ? -wt[q] : wt[q], log2m, lcs);
+                        apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket, sb ? -w0 : w0,
+                                          log2m, lcs);
+                        p61_row_bs<NF, STRAT == STRAT_POWER_SUM_ANY_R>(xp[1], pc, r, mask, a.arb_r,
+                                                                       bucket, sb);
+                        apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket, sb ? -w1 : w1,
+                                          log2m, lcs);
                     }
                 }
             } else {
@@ -872,6 +884,40 @@ __global__ void __launch_bounds__(256) k_gtable_drain(const UpdateArgs a) {
         const typename Ops::key_t key = (typename Ops::key_t)k;
         update_big_key<F, NF>(Ops::prep(key), c, a.coef_dev, a.t, a.k, a.log2m, a.arb_r,
                               a.counters);
+    }
+}
+
+// The same drain for p = 2^61-1, k = 4 and compile-time t: each held key's
+// rows by the signed-digit power sum (row_sd, x^2 and x^3 once per key) with
+// the coefficients in the parameter space, as in the update kernels, so the
+// drain waits on its slot loads and counter atomics only.
+template <int T, int NF, bool ANY>
+__global__ void __launch_bounds__(256) k_gtable_drain_sd(const UpdateArgs a,
+                                                         const ParamCoef<msf::P61, NF * T, 4> pc) {
+    const u32 slots = 1u << a.glog2;
+    const u32 lane = threadIdx.x & 31u;
+    const int log2m = a.log2m;
+    const u32 mask = (1u << log2m) - 1u;
+    for (u32 i0 = blockIdx.x * blockDim.x; i0 < slots; i0 += gridDim.x * blockDim.x) {
+        const u32 i = i0 + threadIdx.x;
+        const u64 k = i < slots ? a.gkeys[i] : DEDUP_EMPTY;
+        const bool held = k != DEDUP_EMPTY;
+        if (a.hashed) {
+            const u32 b = __ballot_sync(0xffffffffu, held);
+            if (lane == 0 && b) atomicAdd(a.hashed, (unsigned long long)__popc(b));
+        }
+        if (!held) continue;
+        const int c = a.gcounts[i];
+        a.gkeys[i] = DEDUP_EMPTY;
+        a.gcounts[i] = 0;
+        msf::P61::Pow3 xp;
+        msf::P61::powers3(k, xp);
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            u32 bucket, sb;
+            p61_row_bs<NF, ANY>(xp, pc, r, mask, a.arb_r, bucket, sb);
+            global_add64(a.counters + ((u64)r << log2m) + bucket, sb ? -(long long)c : (long long)c);
+        }
     }
 }
 

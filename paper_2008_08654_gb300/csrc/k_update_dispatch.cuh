@@ -182,13 +182,39 @@ cudaError_t launch_update_for(const UpdateArgs& a, const u64* coef_host, const L
 }
 
 // The second-level table's drain (one-word keys only: 2^89-1 never uses it).
+// The 2^61-1, k = 4, t = 5 or 7 drain (signed-digit rows, coefficients in
+// the parameter space).
+template <int T, int NF, bool ANY>
+static cudaError_t drain_sd(const UpdateArgs& a, const u64* coef_host, unsigned blocks,
+                            cudaStream_t stream) {
+    ParamCoef<msf::P61, NF * T, 4> pc;
+    fill_param_coef<msf::P61, NF * T, 4>(pc, coef_host);
+    k_gtable_drain_sd<T, NF, ANY><<<blocks, 256, 0, stream>>>(a, pc);
+    return cudaGetLastError();
+}
+
 template <class F>
-cudaError_t launch_gtable_drain_for(const UpdateArgs& a, cudaStream_t stream) {
+cudaError_t launch_gtable_drain_for(const UpdateArgs& a, const u64* coef_host, cudaStream_t stream) {
     if constexpr (!DedupKey<typename FieldOps<F>::key_t>::OK) {
         return cudaErrorInvalidValue;
     } else {
         const u32 slots = 1u << a.glog2;
         const unsigned blocks = (unsigned)((slots + 255u) / 256u < 4096u ? (slots + 255u) / 256u : 4096u);
+        if constexpr (std::is_same<F, msf::P61>::value) {
+            if (a.k == 4 && (a.t == 5 || a.t == 7)) {
+                const bool two = a.mode == CS_TWO_POLY, any = a.arb_r != 0;
+                if (a.t == 5) {
+                    if (two) return any ? drain_sd<5, 2, true>(a, coef_host, blocks, stream)
+                                        : drain_sd<5, 2, false>(a, coef_host, blocks, stream);
+                    return any ? drain_sd<5, 1, true>(a, coef_host, blocks, stream)
+                               : drain_sd<5, 1, false>(a, coef_host, blocks, stream);
+                }
+                if (two) return any ? drain_sd<7, 2, true>(a, coef_host, blocks, stream)
+                                    : drain_sd<7, 2, false>(a, coef_host, blocks, stream);
+                return any ? drain_sd<7, 1, true>(a, coef_host, blocks, stream)
+                           : drain_sd<7, 1, false>(a, coef_host, blocks, stream);
+            }
+        }
         if (a.mode == CS_TWO_POLY)
             k_gtable_drain<F, 2><<<blocks, 256, 0, stream>>>(a);
         else

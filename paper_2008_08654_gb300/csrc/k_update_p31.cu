@@ -9,8 +9,9 @@ cudaError_t launch_update_p31(const UpdateArgs& a, const u64* coef_host, const L
     return launch_update_for<msf::P31>(a, coef_host, cfg, stream, specialized, occupancy);
 }
 
-cudaError_t launch_gtable_drain_p31(const UpdateArgs& a, cudaStream_t stream) {
-    return launch_gtable_drain_for<msf::P31>(a, stream);
+cudaError_t launch_gtable_drain_p31(const UpdateArgs& a, const u64* coef_host,
+                                    cudaStream_t stream) {
+    return launch_gtable_drain_for<msf::P31>(a, coef_host, stream);
 }
 
 }  // namespace msk

@@ -766,7 +766,8 @@ extern "C" ms_status cs_update(cs_sketch* sk, const void* keys_dev, const int32_
     MS_CUDA(msk::launch_cs_update(sk->prime, a, sk->words.data(), cfg, (cudaStream_t)stream, &spec),
             "cs_update");
     if (a.glog2)
-        MS_CUDA(msk::launch_gtable_drain(sk->prime, a, (cudaStream_t)stream), "cs_update drain");
+        MS_CUDA(msk::launch_gtable_drain(sk->prime, a, sk->words.data(), (cudaStream_t)stream),
+                "cs_update drain");
     if (a.replicas)
         MS_CUDA(msk::launch_reduce_replicas(sk->counters, sk->replicas, cfg.replicas,
                                             (u64)sk->t * sk->m, (cudaStream_t)stream),
@@ -838,7 +839,7 @@ extern "C" ms_status cs_update_host(cs_sketch* sk, const void* keys_host, const 
         MS_CUDA(msk::launch_cs_update(sk->prime, a, sk->words.data(), cfg, st, &spec), "cs_update_host");
         MS_CUDA(cudaEventRecord(sk->hfree[buf], st), "cs_update_host");
     }
-    if (a.glog2) MS_CUDA(msk::launch_gtable_drain(sk->prime, a, st), "cs_update_host drain");
+    if (a.glog2) MS_CUDA(msk::launch_gtable_drain(sk->prime, a, sk->words.data(), st), "cs_update_host drain");
     if (a.replicas)
         MS_CUDA(msk::launch_reduce_replicas(sk->counters, sk->replicas, cfg.replicas,
                                             (u64)sk->t * sk->m, st),

@@ -83,9 +83,12 @@ inline bool update_uses_lean_tile(int prime, const UpdateArgs& a, int place, int
 }
 
 // Second-level key table: hashes every key it holds with its count into the
-// int64 counters (t rows, Horner from coef_dev, the split of the sketch's
-// mode) and empties the table for the next update.
-cudaError_t launch_gtable_drain(int prime, const UpdateArgs& a, cudaStream_t stream);
+// int64 counters (t rows, the split of the sketch's mode) and empties the
+// table for the next update.  2^61-1 with k = 4 and t = 5 or 7: signed-digit
+// rows with the coefficients from coef_host in the parameter space; else
+// Horner from coef_dev.
+cudaError_t launch_gtable_drain(int prime, const UpdateArgs& a, const u64* coef_host,
+                                cudaStream_t stream);
 
 // Launch configuration chosen on the host.
 struct LaunchCfg {
@@ -118,10 +121,14 @@ cudaError_t launch_update_p89(const UpdateArgs& a, const u64* coef_host, const L
                               cudaStream_t stream, int* specialized, int* occupancy);
 cudaError_t launch_update_p64(const UpdateArgs& a, const u64* coef_host, const LaunchCfg& cfg,
                               cudaStream_t stream, int* specialized, int* occupancy);
-cudaError_t launch_gtable_drain_p31(const UpdateArgs& a, cudaStream_t stream);
-cudaError_t launch_gtable_drain_p61(const UpdateArgs& a, cudaStream_t stream);
-cudaError_t launch_gtable_drain_p64(const UpdateArgs& a, cudaStream_t stream);
-cudaError_t launch_gtable_drain_p89(const UpdateArgs& a, cudaStream_t stream);
+cudaError_t launch_gtable_drain_p31(const UpdateArgs& a, const u64* coef_host,
+                                    cudaStream_t stream);
+cudaError_t launch_gtable_drain_p61(const UpdateArgs& a, const u64* coef_host,
+                                    cudaStream_t stream);
+cudaError_t launch_gtable_drain_p64(const UpdateArgs& a, const u64* coef_host,
+                                    cudaStream_t stream);
+cudaError_t launch_gtable_drain_p89(const UpdateArgs& a, const u64* coef_host,
+                                    cudaStream_t stream);
 
 struct F2Args {
     const long long* counters;

@@ -94,6 +94,12 @@ CASES = [
     (61, 1, 7, 1 << 16, 4, 0, 0),                      # Horner
     (61, 1, 5, 1 << 15, 4, oracle.TWO_POLY, 1),        # two polynomials
     (61, 1, 5, 50000, 4, oracle.ANY_R, 1),             # any m (Algorithm Mersenne-arb-r)
+    # the remaining compile-time shapes of the 2^61-1 second-level drain
+    (61, 1, 5, 1 << 14, 4, 0, 1),
+    (61, 1, 5, 30000, 4, oracle.ANY_R | oracle.TWO_POLY, 1),
+    (61, 1, 7, 1 << 15, 4, oracle.TWO_POLY, 1),
+    (61, 1, 7, 40000, 4, oracle.ANY_R, 1),
+    (61, 1, 7, 30000, 4, oracle.ANY_R | oracle.TWO_POLY, 1),
     (61, 1, 3, 1 << 17, 2, 0, -1),                     # generic kernel (runtime t, k)
     (61, 1, 9, 1 << 15, 5, oracle.TWO_POLY, -1),       # generic, two polynomials
     (64, 59, 7, 1 << 15, 4, 0, -1),                    # 2^64 - 59
