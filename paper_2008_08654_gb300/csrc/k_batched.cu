@@ -107,41 +107,98 @@ __global__ void __launch_bounds__(1024) k_cs_update_batched(const BatchArgs a) {
                 big[q] = !use_tile || aw > w_safe;
             }
             if constexpr (PS) {
-                // one key at a time (its powers, then the item's rows): few live
-                // registers, so up to 1024 threads per block
-                const u32 tbase = (u32)__cvta_generic_to_shared(tile);
                 const u32 row_bytes = 4u << log2m;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int w = wt[q];
-                    if (w == 0) continue;  // ragged end of the chunk
-                    const bool bq = big[q];
-                    msf::P61::Pow3 xp;
-                    msf::P61::powers3(key[q], xp);
-                    auto row = [&](int r) {
-                        const PsCoef cb = sps[(r - r0) * NF];
-                        u32 ylo, yhi;
-                        msf::P61::row_sd(xp, cb.cl, cb.ch, cb.nd, cb.k1, a.c2p31, ylo, yhi);
-                        const u32 bucket = ylo & mask;
-                        if (MODE == CS_TWO_POLY) {
-                            const PsCoef cs = sps[(r - r0) * NF + 1];
-                            msf::P61::row_sd(xp, cs.cl, cs.ch, cs.nd, cs.k1, a.c2p31, ylo, yhi);
+                const int nr = r1 - r0;
+                // A key that goes to the int64 counters (every key of a direct
+                // item; in a tile item the rare key whose weight could overflow
+                // an int32 cell): its rows one at a time.  Rolled over the four
+                // keys (their registers rotate), so the cold path stays small.
+                if (big[0] | big[1] | big[2] | big[3]) {
+#pragma unroll 1
+                    for (int q = 0; q < 4; ++q) {
+                        // key 0 is taken here (its weight then 0 for the tile
+                        // path) and moves to the back: after four turns the
+                        // keys are in their places again
+                        const u64 kq = (u64)key[0];
+                        const int wq = big[0] ? wt[0] : 0;
+                        const int wk = big[0] ? 0 : wt[0];
+                        key[0] = key[1];
+                        key[1] = key[2];
+                        key[2] = key[3];
+                        key[3] = (typename Ops::key_t)kq;
+                        wt[0] = wt[1];
+                        wt[1] = wt[2];
+                        wt[2] = wt[3];
+                        wt[3] = wk;
+                        big[0] = big[1];
+                        big[1] = big[2];
+                        big[2] = big[3];
+                        big[3] = false;
+                        if (wq == 0) continue;
+                        msf::P61::Pow3 xp;
+                        msf::P61::powers3(kq, xp);
+#pragma unroll 1
+                        for (int rr = 0; rr < nr; ++rr) {
+                            const PsCoef cb = sps[rr * NF];
+                            u32 ylo, yhi;
+                            msf::P61::row_sd(xp, cb.cl, cb.ch, cb.nd, cb.k1, a.c2p31, ylo, yhi);
+                            const u32 bucket = ylo & mask;
+                            if (MODE == CS_TWO_POLY) {
+                                const PsCoef cs = sps[rr * NF + 1];
+                                msf::P61::row_sd(xp, cs.cl, cs.ch, cs.nd, cs.k1, a.c2p31, ylo, yhi);
+                            }
+                            global_add64(job.counters + (((u64)(r0 + rr)) << log2m) + bucket,
+                                         (yhi & 0x10000000u) ? -(long long)wq : (long long)wq);
                         }
-                        const int d = (yhi & 0x10000000u) ? -w : w;  // bit 60 of the residue
-                        if (bq)
-                            global_add64(job.counters + (((u64)r) << log2m) + bucket, (long long)d);
-                        else
-                            asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(tbase + (u32)(r - r0) * row_bytes + (bucket << 2)),
-                                         "r"(d)
+                    }
+                }
+                if (use_tile) {
+                    // Two keys at a time, so each row's coefficients are read from
+                    // shared memory once for both; a zero weight adds 0.
+                    const u32 tbase = (u32)__cvta_generic_to_shared(tile);
+#pragma unroll 1
+                    for (int qq = 0; qq < 2; ++qq) {
+                        msf::P61::Pow3 xa, xb;
+                        msf::P61::powers3(key[0], xa);
+                        msf::P61::powers3(key[1], xb);
+                        const int wa = wt[0], wb = wt[1];
+                        key[0] = key[2];
+                        key[1] = key[3];
+                        wt[0] = wt[2];
+                        wt[1] = wt[3];
+                        auto row = [&](int rr, u32 rbase) {
+                            const PsCoef cb = sps[rr * NF];
+                            u32 alo, ahi, blo, bhi;
+                            msf::P61::row_sd(xa, cb.cl, cb.ch, cb.nd, cb.k1, a.c2p31, alo, ahi);
+                            msf::P61::row_sd(xb, cb.cl, cb.ch, cb.nd, cb.k1, a.c2p31, blo, bhi);
+                            const u32 ba = alo & mask, bb = blo & mask;
+                            if (MODE == CS_TWO_POLY) {
+                                const PsCoef cs = sps[rr * NF + 1];
+                                msf::P61::row_sd(xa, cs.cl, cs.ch, cs.nd, cs.k1, a.c2p31, alo, ahi);
+                                msf::P61::row_sd(xb, cs.cl, cs.ch, cs.nd, cs.k1, a.c2p31, blo, bhi);
+                            }
+                            const int da = (ahi & 0x10000000u) ? -wa : wa;  // bit 60 of the residue
+                            const int db = (bhi & 0x10000000u) ? -wb : wb;
+                            asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(rbase + (ba << 2)), "r"(da)
                                          : "memory");
-                    };
-                    if (r1 - r0 == 5) {
-                        // five rows (every item of a t = 5 sketch): unrolled, so
-                        // the rows' multiply chains interleave
+                            asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(rbase + (bb << 2)), "r"(db)
+                                         : "memory");
+                        };
+                        u32 rbase = tbase;  // shared address of the item's row rr
+                        if (nr == 5) {
+                            // five rows (every item of a t = 5 sketch): unrolled, so
+                            // the rows' multiply chains interleave
 #pragma unroll
-                        for (int rr = 0; rr < 5; ++rr) row(r0 + rr);
-                    } else {
-                        for (int r = r0; r < r1; ++r) row(r);
+                            for (int rr = 0; rr < 5; ++rr) {
+                                row(rr, rbase);
+                                rbase += row_bytes;
+                            }
+                        } else {
+                            for (int rr = 0; rr < nr; ++rr) {
+                                row(rr, rbase);
+                                rbase += row_bytes;
+                            }
+                        }
                     }
                 }
             } else {
