@@ -106,6 +106,16 @@ extern "C" ms_status cs_batch_create(cs_batch** out, const cs_batch_job* jobs_ho
             max_t = std::max(max_t, sk->t);
         }
     }
+    // Longest streams first: the persistent blocks take work items in table
+    // order, so the items handed out last are the short ones and no block is
+    // left with a whole chunk after the others have run out of work.
+    std::stable_sort(table.begin(), table.end(),
+                     [](const msk::BatchJobDev& x, const msk::BatchJobDev& y) { return x.n > y.n; });
+    u64 first = 0;
+    for (msk::BatchJobDev& d : table) {
+        d.first_item = (u32)first;
+        first += ((d.n + tu.chunk_keys - 1) / tu.chunk_keys) * (u64)((d.t + rpi_req - 1) / rpi_req);
+    }
     const int rpi = std::min(rpi_req, max_t);
 
     cs_batch* b = new (std::nothrow) cs_batch;

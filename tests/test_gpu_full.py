@@ -43,6 +43,16 @@ def test_plain_sketch_full_size():
     _run("plain")
 
 
+@pytest.mark.parametrize("n", [(1 << 20) - 3, 3 * (1 << 19) + 1, (1 << 21) + 5])
+def test_plain_sketch_balanced_launch_sizes(n):
+    """Streams of two or three rounds of four keys a thread, for which the
+    automatic launch sizes its blocks so every thread takes the same number of
+    rounds; ragged ends included."""
+    launch = _run("plain", n=n)
+    assert launch["specialized"] == 2  # the lean shared-memory tile kernel
+    assert launch["blocks"] * launch["threads"] * 4 * 3 >= n
+
+
 def test_large_sketch_full_size():
     launch = _run("large")
     print("large sketch launch:", launch)
