@@ -35,8 +35,8 @@ def _jobs(torch, ms, nsk, seed, b=61, c=1, k=4, mode=0, ts=(3, 5), ms_=(256, 102
         t = int(rng.choice(ts))
         m = int(rng.choice(ms_))
         n = int(10 ** rng.uniform(0, np.log10(nmax)))
-        if i == 0:
-            n = 0  # an empty job
+        if i == 0 or i == nsk // 2:
+            n = 0  # empty jobs (the plan orders jobs by length, so these move to its end)
         s = seed * 1000 + i
         if b == 31:
             keys = datagen.u32_below(s, 0, n)
