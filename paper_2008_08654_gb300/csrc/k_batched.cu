@@ -185,9 +185,11 @@ __global__ void __launch_bounds__(1024) k_cs_update_batched(const BatchArgs a) {
                                          : "memory");
                         };
                         u32 rbase = tbase;  // shared address of the item's row rr
-                        if (nr == 5) {
+                        if (MODE != CS_TWO_POLY && nr == 5) {
                             // five rows (every item of a t = 5 sketch): unrolled, so
-                            // the rows' multiply chains interleave
+                            // the rows' multiply chains interleave (with two
+                            // polynomials a row has four chains already, and the
+                            // unrolled rows spilled)
 #pragma unroll
                             for (int rr = 0; rr < 5; ++rr) {
                                 row(rr, rbase);

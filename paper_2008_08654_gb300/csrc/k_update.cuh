@@ -319,22 +319,43 @@ __device__ __forceinline__ bool dedup_count(u64* tk, int* tc, int log2slots, u64
     return true;
 }
 
-// Second-level table in global memory (L2-resident): counts c occurrences of
-// `key` when its slot holds it or was free (claimed here); false otherwise.
-// `cur` is the slot's key as loaded before (so that a warp's loads overlap).
+// Second-level table in global memory (L2-resident), two-way: a key's place is
+// the aligned pair of slots at `base` (the slot hash with its low bit
+// cleared).  gtable_count2 counts c occurrences of `key` when either slot holds
+// it or one was free (claimed here, the pair's first slot first); false
+// otherwise.  cur0, cur1 are the pair's keys as loaded before by one 16-byte
+// load (so that a warp's loads overlap).  Should a key ever hold both slots,
+// each count is still hashed with its key, so the result stays exact.
 __device__ __forceinline__ u32 gtable_slot(u64 key, int glog2) {
     return (u32)((key * 0xD6E8FEB86659FD93ull) >> (64 - glog2));
 }
-__device__ __forceinline__ bool gtable_count(unsigned long long* gk, int* gc, u32 slot, u64 key,
-                                             u64 cur, int c) {
+
+__device__ __forceinline__ bool gtable_count2(unsigned long long* gk, int* gc, u32 base, u64 key,
+                                              u64 cur0, u64 cur1, int c) {
     if (key == DEDUP_EMPTY) return false;
-    if (cur == DEDUP_EMPTY) {
-        cur = atomicCAS(gk + slot, DEDUP_EMPTY, (unsigned long long)key);
-        if (cur == DEDUP_EMPTY) cur = key;  // claimed by this thread
+    if (cur0 == key) {
+        atomicAdd(gc + base, c);
+        return true;
     }
-    if (cur != key) return false;
-    atomicAdd(gc + slot, c);
-    return true;
+    if (cur1 == key) {
+        atomicAdd(gc + base + 1, c);
+        return true;
+    }
+    if (cur0 == DEDUP_EMPTY) {
+        cur0 = atomicCAS(gk + base, DEDUP_EMPTY, (unsigned long long)key);
+        if (cur0 == DEDUP_EMPTY || cur0 == key) {
+            atomicAdd(gc + base, c);
+            return true;
+        }
+    }
+    if (cur1 == DEDUP_EMPTY) {
+        cur1 = atomicCAS(gk + base + 1, DEDUP_EMPTY, (unsigned long long)key);
+        if (cur1 == DEDUP_EMPTY || cur1 == key) {
+            atomicAdd(gc + base + 1, c);
+            return true;
+        }
+    }
+    return false;
 }
 
 // ------------------------------------------------------------ cluster helpers
@@ -615,17 +636,19 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                         miss[q] = wt[q] != 0 && !dedup_count(tk, tc, dd_log2, (u64)key[q], wt[q]);
                     if (a.glog2) {
                         // the block's misses try the second-level table (the four
-                        // slot loads of a lane are in flight together)
+                        // slot-pair loads of a lane are in flight together)
                         u32 gs[4];
-                        u64 gcur[4];
+                        ulonglong2 gcur[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            gs[q] = gtable_slot((u64)key[q], a.glog2);
-                            gcur[q] = miss[q] ? __ldcg(a.gkeys + gs[q]) : DEDUP_EMPTY;
+                            gs[q] = gtable_slot((u64)key[q], a.glog2) & ~1u;
+                            gcur[q] = miss[q] ? __ldcg(reinterpret_cast<const ulonglong2*>(a.gkeys + gs[q]))
+                                              : make_ulonglong2(DEDUP_EMPTY, DEDUP_EMPTY);
                         }
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
-                            if (miss[q] && gtable_count(a.gkeys, a.gcounts, gs[q], (u64)key[q], gcur[q], wt[q]))
+                            if (miss[q] && gtable_count2(a.gkeys, a.gcounts, gs[q], (u64)key[q], gcur[q].x,
+                                                         gcur[q].y, wt[q]))
                                 miss[q] = false;
                     }
 #pragma unroll
