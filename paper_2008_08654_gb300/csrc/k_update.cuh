@@ -960,8 +960,14 @@ __global__ void __launch_bounds__(256) k_gtable_drain_sd(const UpdateArgs a,
 // r * 2^log2m + b).  The t = 5 two-for-one kernels are capped at 42 registers
 // (three 512-thread blocks per SM), the others at 64.  With unit weights the
 // four keys go through a rolled loop (their registers rotate): unrolled, the
-// compiler interleaves them and spills.
-template <int T, int MODE, bool WEIGHTED, int LOG2M>
+// compiler interleaves them and spills.  ANY: any number of buckets r
+// (Algorithm Mersenne-arb-r, Sec. 3.3) in rows 2^log2m >= r wide: with h the
+// canonical residue and h + 1 = a 2^60 + j (j < 2^60), the bucket is
+// floor(r j / 2^60) -- taken here from j's 28- and 32-bit halves as
+// floor((j_hi r + floor(j_lo r / 2^32)) / 2^28), the same integer -- and the
+// update is subtracted when a = 0 (two polynomials: the sign is still bit 60
+// of the second one).
+template <int T, int MODE, bool WEIGHTED, int LOG2M, bool ANY = false>
 __global__ void __launch_bounds__(512, (MODE != CS_TWO_POLY && T == 5) ? 3 : 2)
 k_cs_update_tile(const UpdateArgs a,
                  const ParamCoef<msf::P61, (MODE == CS_TWO_POLY ? 2 : 1) * T, 4> pc) {
@@ -1015,8 +1021,8 @@ k_cs_update_tile(const UpdateArgs a,
             wt[1] = wt[2];
             wt[2] = wt[3];
             if (WEIGHTED && (u32)w + w_safe > 2u * w_safe) {  // |w| > w_safe (w_safe < 2^31)
-                update_big_key<F, NF>(FieldOps<F>::prep(kq), w, a.coef_dev, T, 4, log2m, 0u,
-                                      a.counters);
+                update_big_key<F, NF>(FieldOps<F>::prep(kq), w, a.coef_dev, T, 4, log2m,
+                                      ANY ? a.arb_r : 0u, a.counters);
                 continue;
             }
             F::Pow3 xp;
@@ -1026,11 +1032,23 @@ k_cs_update_tile(const UpdateArgs a,
                 u32 ylo, yhi;
                 F::row_sd(xp, pc.cl + 3 * NF * r, pc.ch + 3 * NF * r, pc.nd + 3 * NF * r,
                           pc.k1[NF * r], pc.c2p31, ylo, yhi);
-                const u32 bucket = ylo & mask;
+                u32 bucket, keep = 0;
+                if constexpr (ANY) {
+                    const u32 hlo = ylo + 1u;  // h + 1 = (hhi : hlo), h < 2^61 - 1
+                    const u32 hhi = (yhi & 0x1FFFFFFFu) + (hlo == 0u ? 1u : 0u);
+                    bucket = (u32)(((u64)(hhi & 0x0FFFFFFFu) * a.arb_r + __umulhi(hlo, a.arb_r)) >> 28);
+                    keep = hhi >> 28;  // a: add when 1, subtract when 0
+                } else {
+                    bucket = ylo & mask;
+                }
                 if (NF == 2)  // the sign from the second polynomial's bit 60
                     F::row_sd(xp, pc.cl + 3 * (2 * r + 1), pc.ch + 3 * (2 * r + 1),
                               pc.nd + 3 * (2 * r + 1), pc.k1[2 * r + 1], pc.c2p31, ylo, yhi);
-                const int d = (yhi & 0x10000000u) ? -w : w;  // bit 60 of the residue
+                int d;
+                if (ANY && NF == 1)
+                    d = keep ? w : -w;
+                else
+                    d = (yhi & 0x10000000u) ? -w : w;  // bit 60 of the residue
                 asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(base + (u32)r * row_bytes + (bucket << 2)),
                              "r"(d)
                              : "memory");

@@ -69,8 +69,15 @@ static cudaError_t launch_exact(const UpdateArgs& a, const u64* coef_host, const
                                 cudaStream_t stream, int* occupancy) {
     constexpr int NF = (MODE == CS_TWO_POLY) ? 2 : 1;
     auto kern = k_cs_update<F, T, K, MODE, PLACE, STRAT>;
-    // 2^61-1, k = 4, shared-memory tile, power-of-two buckets: the lean kernel
-    // (the statistics hook counts entries only in the general one)
+    // 2^61-1, k = 4, shared-memory tile: the lean kernel (the statistics hook
+    // counts entries only in the general one)
+    if constexpr (std::is_same<F, msf::P61>::value && T > 0 && K == 4 && PLACE == PLACE_SMEM &&
+                  STRAT == STRAT_POWER_SUM_ANY_R) {
+        // any number of buckets: the lean kernel with the any-m map, run-time row stride
+        if (update_uses_lean_tile(PRIME_61, a, cfg.place, cfg.strategy))
+            kern = a.weights ? k_cs_update_tile<T, MODE, true, 0, true>
+                             : k_cs_update_tile<T, MODE, false, 0, true>;
+    }
     if constexpr (std::is_same<F, msf::P61>::value && T > 0 && K == 4 && PLACE == PLACE_SMEM &&
                   STRAT == STRAT_POWER_SUM) {
         if (update_uses_lean_tile(PRIME_61, a, cfg.place, cfg.strategy)) {

@@ -75,11 +75,11 @@ inline bool update_is_specialized(int prime, int t, int k, u32 arb_r) {
 
 // Whether a specialized 2^61-1 update with a shared-memory tile runs the lean
 // one-key-a-thread kernel (k_cs_update_tile) rather than the general one:
-// power-of-two buckets, no statistics hook, no request for the general kernel.
+// power-of-two or any number of buckets, no statistics hook, no request for
+// the general kernel.
 inline bool update_uses_lean_tile(int prime, const UpdateArgs& a, int place, int strategy) {
     return prime == PRIME_61 && a.k == 4 && (a.t == 5 || a.t == 7) && place == PLACE_SMEM &&
-           strategy == STRAT_POWER_SUM && a.arb_r == 0 && a.hashed == nullptr &&
-           a.keys_per_thread_hint == 0;
+           strategy == STRAT_POWER_SUM && a.hashed == nullptr && a.keys_per_thread_hint == 0;
 }
 
 // Second-level key table: hashes every key it holds with its count into the

@@ -31,6 +31,8 @@ CASES = [
     (61, 1, 7, 50000, 4, ANY, 3, "pm100"),        # direct int64 atomics
     (61, 1, 5, 6000, 4, ANY, 1, "pm100"),         # distributed shared memory
     (61, 1, 5, 1000, 4, ANY | TP, -1, "pm100"),   # two polynomials
+    (61, 1, 7, 3000, 4, ANY, 0, "unit"),          # seven rows in the shared-memory tile
+    (61, 1, 7, 2000, 4, ANY | TP, 0, "pm100"),
     (61, 1, 3, 12345, 2, ANY | TP, 2, "unit"),
     (61, 1, 1, (1 << 24) - 1, 4, ANY, -1, "unit"),  # largest m
     (61, 1, 15, 7, 1, ANY, -1, "pm100"),          # constant hash
