@@ -523,9 +523,15 @@ __device__ __forceinline__ void update_big_key(const typename FieldOps<F>::Prep&
 // T, K > 0: compile-time rows and degree with ParamCoef; T = K = 0: runtime t
 // and k with coefficients staged from coef_dev into shared memory.
 // Two-for-one kernels are capped at 64 registers (two 512-thread blocks per SM);
-// two-polynomial kernels keep twice the key state live and get 128.
+// two-polynomial kernels keep twice the key state live and get 128, except for
+// 2^61-1 in global placement, where the kernel waits on memory and two blocks
+// per SM at 64 registers (a few spilled words) were 15% faster on the 2^28-key
+// Zipf sketch (2.90 vs 3.41 ms); the wider primes' rows would spill far more.
 template <class F, int T, int K, int MODE, int PLACE, int STRAT>
-__global__ void __launch_bounds__(512, (MODE == CS_TWO_POLY) ? 1 : 2)
+__global__ void __launch_bounds__(512, (MODE == CS_TWO_POLY &&
+                                        !(PLACE == PLACE_GLOBAL && std::is_same<F, msf::P61>::value))
+                                           ? 1
+                                           : 2)
 k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1) * T, K> pc) {
     typedef FieldOps<F> Ops;
     typedef typename Ops::val_t val_t;
