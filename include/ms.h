@@ -339,7 +339,9 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  *            shared-memory tile in the general kernel (four keys a thread)
  *            instead of the lean one (one key a thread; the default there).
  *            All give identical hash values.
- *  threads (multiple of 32, <= 512; default 512, 256 for place 1), blocks
+ *  threads (multiple of 32, <= 512; default 512, 256 for place 1; the lean
+ *  kernel on a stream of two or three rounds of four keys a thread takes one
+ *  wave of blocks with the threads sized for equal rounds), blocks
  *  (total), blocks_per_sm (cap), cluster (power of two <= 16, place 1 only),
  *  replicas (power of two <= 32, place 2 only; capped at the replicas the
  *  sketch owns; default 16),
@@ -352,7 +354,8 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  *  the keys of its 17th to 32nd chunks of 128 stops using it.  3 = as 2, and a
  *  key the block's table misses is counted in a second-level table of 2^21
  *  keys in global memory (24 MiB, allocated by the sketch on first use and
- *  kept, L2-resident) when it owns or can claim its slot there; after the
+ *  kept, L2-resident) when it owns or can claim one of its two slots there
+ *  (the aligned pair its hash picks); after the
  *  update one kernel hashes each key that table holds once, with its count,
  *  and empties it.  The default uses the second level for streams of at least
  *  2^22 keys (3 forces it for any length).  The counters are identical for
