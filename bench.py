@@ -352,7 +352,7 @@ def hashed_entries(sk, keys, w) -> int:
     return int(hashed_t.item())
 
 
-def plain_2p28_result(args, ms, peaks, hbm_gbs, hbm_src, workload: str = "plain-2^28") -> dict:
+def plain_result(args, ms, peaks, hbm_gbs, hbm_src, workload: str = "plain-2^28") -> dict:
     """The plain distribution (uniform keys below p, weights in [-100, 100], t=5,
     m=1024) at 2^28 keys, where the hot-path target is judged (or, with
     workload="plain", at its specified 2^20 keys, L2 flushed before each step)."""
@@ -534,8 +534,8 @@ def run_ours(args, wl):
         # each timed with its own clock record
         del keys, w, sk
         torch.cuda.empty_cache()
-        line["plain_2p28"] = plain_2p28_result(args, ms, peaks, hbm_gbs, hbm_src)
-        line["plain_2p20"] = plain_2p28_result(args, ms, peaks, hbm_gbs, hbm_src, "plain")
+        line["plain_2p28"] = plain_result(args, ms, peaks, hbm_gbs, hbm_src)
+        line["plain_2p20"] = plain_result(args, ms, peaks, hbm_gbs, hbm_src, "plain")
         line["batched"] = batched_result(args, ms, peaks)
     if world > 1:
         dist.destroy_process_group()
