@@ -525,8 +525,8 @@ __device__ __forceinline__ void update_big_key(const typename FieldOps<F>::Prep&
 // Two-for-one kernels are capped at 64 registers (two 512-thread blocks per SM);
 // two-polynomial kernels keep twice the key state live and get 128, except for
 // 2^61-1 in global placement, where the kernel waits on memory and two blocks
-// per SM at 64 registers (a few spilled words) were 15% faster on the 2^28-key
-// Zipf sketch (2.90 vs 3.41 ms); the wider primes' rows would spill far more.
+// per SM at 64 registers were 15% faster on the 2^28-key Zipf sketch (2.90 vs
+// 3.41 ms); the wider primes' rows would spill at 64.
 template <class F, int T, int K, int MODE, int PLACE, int STRAT>
 __global__ void __launch_bounds__(512, (MODE == CS_TWO_POLY &&
                                         !(PLACE == PLACE_GLOBAL && std::is_same<F, msf::P61>::value))
@@ -738,7 +738,32 @@ k_cs_update(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1)
                     wt[q] = 0;
                 }
             }
-            if constexpr (PLACE == PLACE_GLOBAL) {
+            if constexpr (PLACE == PLACE_GLOBAL && NF == 2) {
+                // two polynomials: one key's powers live at a time (a rolled
+                // loop over the four keys, whose registers rotate), so the
+                // kernel fits 64 registers without spilling (6% faster on the
+                // 2^28-key Zipf sketch than two keys at a time)
+#pragma unroll 1
+                for (int q = 0; q < 4; ++q) {
+                    msf::P61::Pow3 xs;
+                    msf::P61::powers3(key[0], xs);
+                    const int ws = wt[0];
+                    key[0] = key[1];
+                    key[1] = key[2];
+                    key[2] = key[3];
+                    wt[0] = wt[1];
+                    wt[1] = wt[2];
+                    wt[2] = wt[3];
+#pragma unroll
+                    for (int r = 0; r < T; ++r) {
+                        u32 bucket, sb;
+                        p61_row_bs<NF, STRAT == STRAT_POWER_SUM_ANY_R>(xs, pc, r, mask, a.arb_r,
+                                                                       bucket, sb);
+                        apply_fast<PLACE>(tile, tile_saddr, a.counters, r, bucket, sb ? -ws : ws,
+                                          log2m, lcs);
+                    }
+                }
+            } else if constexpr (PLACE == PLACE_GLOBAL) {
                 // two keys' powers live at a time (a rolled loop over the two
                 // pairs, whose registers rotate; rows outer within a pair): with
                 // all four keys' powers live the de-duplicating path spilled

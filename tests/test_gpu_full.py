@@ -53,6 +53,14 @@ def test_plain_sketch_balanced_launch_sizes(n):
     assert launch["blocks"] * launch["threads"] * 4 * 3 >= n
 
 
+def test_plain_any_m_quarter():
+    """Any number of buckets (m = 1000, Algorithm Mersenne-arb-r) on the first
+    2^26 keys of the 2^28-key stream the bench times, in its launch
+    configuration (the lean kernel with the any-m map)."""
+    launch = _run("plain-anyr", n=1 << 26)
+    assert launch["specialized"] == 2
+
+
 def test_large_sketch_full_size():
     launch = _run("large")
     print("large sketch launch:", launch)
