@@ -515,8 +515,13 @@ def run_ours(args, wl):
         "roofline": roofline,
         "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": "keys/s",
                 "h2d_bytes_per_step": n * bytes_per_key, "d2h_bytes_per_step": 16},
-        # zero, update, (replica reduce,) F2 per timed step
-        "gpu_launches": (4 if launch.get("replicas") else 3) * args.steps,
+        # zero, update, (second-level table drain,) (replica reduce,) F2 per
+        # timed step; the library drains its second-level key table after
+        # de-duplicating updates (unit weights, global placement) of 2^22 keys
+        # or more
+        "gpu_launches": (3 + (1 if launch.get("replicas") else 0)
+                         + (1 if (w is None and launch.get("place") == 2 and launch.get("replicas")
+                                  and n >= 1 << 22) else 0)) * args.steps,
         "f2_estimate": str(f2_est),
     }
     if clk:
