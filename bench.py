@@ -8,7 +8,7 @@ hashing.  One step = zero the counters, cs_update over the whole stream,
 cs_estimate_f2 (every step of the path, in the library's kernels).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload large|large-twopoly|plain|plain-2^28|sweep|batched]
+                  [--workload large|large-twopoly|plain|plain-2^28|sweep|batched|query|...]
 
 `value` is whole-job keys/s with the keys already resident in HBM (2 GiB per
 rank, far larger than the 129 MB L2, so no flush is needed between steps).
@@ -741,6 +741,43 @@ def run_divwide(args):
                  table2=rows, parity="tests/test_gpu_divwide.py")
 
 
+def run_query(args):
+    """Point queries (the f_x estimate, Sec. 1.3): the large sketch (t=7, m=2^16,
+    two-for-one) filled with its 2^28-key Zipf stream, then the estimates of
+    2^26 keys of the same stream (8 B in, 8 B out per key; t rows hashed and t
+    counters gathered per key, then their median)."""
+    import torch
+    import paper_2008_08654_gb300 as ms
+    wl = WORKLOADS["large"]
+    keys_np, _ = make_inputs(wl, args.seed, 0)
+    keys = torch.from_numpy(keys_np.view(np.int64)).cuda()
+    sk = ms.Sketch(t=wl["t"], m=wl["m"], k=4, b=61, c=1, seed=args.seed, mode=0)
+    sk.update(keys)
+    nq = args.keys or (1 << 26)
+    q = keys[:nq].clone()
+    del keys, keys_np
+    torch.cuda.empty_cache()
+    out = torch.empty(nq, dtype=torch.int64, device="cuda")
+    peaks = probe_peaks(ms)
+    hbm_gbs, hbm_src = hbm_peak_gbs()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    t = _timed(lambda: sk.point_query(q, out), max(3, args.steps), max(3, args.warmup))
+    clk = clocks.stop()
+    roof = roofline_8d(nq, wl["t"], 1, 16, t * 1e-3, peaks, hbm_gbs, hbm_src)
+    roof["kernel"] = "k_cs_point_query"
+    line = _line("point queries/s (t=7, m=2^16, p=2^61-1)", nq / (t * 1e-3), "queries/s", args,
+                 {"workload": "%d point queries of the 2^28-key Zipf(1.1) stream's first keys "
+                              "on the large sketch (t=7, m=2^16) filled with that stream" % nq,
+                  "l2": "queried keys (%d MiB) exceed the 129 MB L2; no flush" % (nq * 8 >> 20)},
+                 ms_per_step=t, roofline=roof,
+                 parity="tests/test_gpu_parity.py, tests/test_gpu_anyr.py")
+    if clk:
+        line["clocks"] = clk
+    return line
+
+
 def run_table1(args):
     """The paper's Table 1 workload: 10^7 k-universal hashes of random 64-bit
     keys for k in {2, 4, 8}, p = 2^61-1 and p = 2^89-1 (keys in device memory)."""
@@ -927,7 +964,7 @@ def run_serving(args):
 
 
 EXTRA = {"sweep": run_sweep, "div": run_div, "divwide": run_divwide, "table1": run_table1,
-         "batched": run_batched,
+         "batched": run_batched, "query": run_query,
          "serving": run_serving}
 
 

@@ -254,10 +254,14 @@ static cudaError_t launch_pq(const QueryArgs& a, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_cs_point_query(int prime, const QueryArgs& a, cudaStream_t stream) {
+cudaError_t launch_cs_point_query(int prime, const QueryArgs& a, const u64* coef_host,
+                                  cudaStream_t stream) {
     switch (prime) {
         case PRIME_31: return launch_pq<msf::P31>(a, stream);
-        case PRIME_61: return launch_pq<msf::P61>(a, stream);
+        case PRIME_61:
+            if (a.k == 4 && (a.t == 5 || a.t == 7))
+                return launch_point_query_p61_sd(a, coef_host, stream);
+            return launch_pq<msf::P61>(a, stream);
         case PRIME_89: return launch_pq<msf::P89>(a, stream);
         default: return launch_pq<msf::P64>(a, stream);
     }

@@ -975,6 +975,62 @@ __global__ void __launch_bounds__(256) k_gtable_drain_sd(const UpdateArgs a,
     }
 }
 
+// ------------------------------------------------------------ point queries
+//
+// Point queries for p = 2^61-1, k = 4 and compile-time t: the estimate of f_x
+// is the median over the rows of s_r(x) C[r][i_r(x)] (Sec. 1.3).  Each key's
+// rows by the update kernels' signed-digit power sum (x^2, x^3 once per key,
+// the coefficients in the parameter space), the split of the sketch's mode
+// (ANY: Algorithm Mersenne-arb-r as in the lean kernel), the t estimates in
+// registers, and their median as the estimate of rank t/2 (ties broken by row).
+template <int T, int NF, bool ANY>
+__global__ void __launch_bounds__(256) k_cs_point_query_sd(const QueryArgs a,
+                                                            const ParamCoef<msf::P61, NF * T, 4> pc) {
+    typedef msf::P61 F;
+    const int log2m = a.log2m;
+    const u32 mask = (1u << log2m) - 1u;
+    const u64* keys = reinterpret_cast<const u64*>(a.keys);
+    for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < a.n;
+         j += (u64)gridDim.x * blockDim.x) {
+        F::Pow3 xp;
+        F::powers3(__ldcs(keys + j), xp);
+        long long est[T];
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            u32 ylo, yhi;
+            F::row_sd(xp, pc.cl + 3 * NF * r, pc.ch + 3 * NF * r, pc.nd + 3 * NF * r,
+                      pc.k1[NF * r], pc.c2p31, ylo, yhi);
+            u32 bucket, neg;
+            if constexpr (ANY) {
+                const u32 hlo = ylo + 1u;  // h + 1 = (hhi : hlo), h < 2^61 - 1
+                const u32 hhi = (yhi & 0x1FFFFFFFu) + (hlo == 0u ? 1u : 0u);
+                bucket = (u32)(((u64)(hhi & 0x0FFFFFFFu) * a.arb_r + __umulhi(hlo, a.arb_r)) >> 28);
+                neg = (hhi >> 28) ^ 1u;  // subtract when a = 0
+            } else {
+                bucket = ylo & mask;
+                neg = (yhi >> 28) & 1u;  // bit 60 of the residue
+            }
+            if (NF == 2) {  // the sign from the second polynomial's bit 60
+                F::row_sd(xp, pc.cl + 3 * (2 * r + 1), pc.ch + 3 * (2 * r + 1),
+                          pc.nd + 3 * (2 * r + 1), pc.k1[2 * r + 1], pc.c2p31, ylo, yhi);
+                neg = (yhi >> 28) & 1u;
+            }
+            const long long c = __ldg(a.counters + ((u64)r << log2m) + bucket);
+            est[r] = neg ? -c : c;
+        }
+        long long med = est[0];
+#pragma unroll
+        for (int i = 0; i < T; ++i) {
+            int rank = 0;
+#pragma unroll
+            for (int q = 0; q < T; ++q)
+                rank += (est[q] < est[i] || (est[q] == est[i] && q < i)) ? 1 : 0;
+            if (rank == T / 2) med = est[i];
+        }
+        a.out[j] = med;
+    }
+}
+
 // ------------------------------------------------------------ lean tile kernel
 //
 // The hot configuration on its own: p = 2^61-1, k = 4 (signed-digit power

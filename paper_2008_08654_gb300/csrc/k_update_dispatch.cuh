@@ -200,6 +200,18 @@ static cudaError_t drain_sd(const UpdateArgs& a, const u64* coef_host, unsigned 
     return cudaGetLastError();
 }
 
+// Point queries, 2^61-1 with k = 4 and t = 5 or 7 (the signed-digit rows).
+template <int T, int NF, bool ANY>
+static cudaError_t point_query_sd(const QueryArgs& a, const u64* coef_host, cudaStream_t stream) {
+    ParamCoef<msf::P61, NF * T, 4> pc;
+    fill_param_coef<msf::P61, NF * T, 4>(pc, coef_host);
+    const int threads = 256;
+    u64 blocks = (a.n + threads - 1) / threads;
+    if (blocks > 4096) blocks = 4096;
+    k_cs_point_query_sd<T, NF, ANY><<<(unsigned)blocks, threads, 0, stream>>>(a, pc);
+    return cudaGetLastError();
+}
+
 template <class F>
 cudaError_t launch_gtable_drain_for(const UpdateArgs& a, const u64* coef_host, cudaStream_t stream) {
     if constexpr (!DedupKey<typename FieldOps<F>::key_t>::OK) {

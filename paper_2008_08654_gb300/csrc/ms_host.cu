@@ -906,7 +906,8 @@ extern "C" ms_status cs_point_query(const cs_sketch* sk, const void* keys_dev, i
     a.mode = sk->mode & CS_TWO_POLY;
     a.arb_r = sk->r;
     a.out = (long long*)out_dev;
-    MS_CUDA(msk::launch_cs_point_query(sk->prime, a, (cudaStream_t)stream), "cs_point_query");
+    MS_CUDA(msk::launch_cs_point_query(sk->prime, a, sk->words.data(), (cudaStream_t)stream),
+            "cs_point_query");
     return MS_OK;
 }
 

@@ -151,7 +151,13 @@ struct QueryArgs {
     u32 arb_r;  // as in UpdateArgs
     long long* out;
 };
-cudaError_t launch_cs_point_query(int prime, const QueryArgs& a, cudaStream_t stream);
+// coef_host: the sketch's coefficient limbs (2^61-1 with k = 4 and t = 5 or 7
+// run the signed-digit rows with them in the parameter space; the others
+// Horner from coef_dev).
+cudaError_t launch_cs_point_query(int prime, const QueryArgs& a, const u64* coef_host,
+                                  cudaStream_t stream);
+cudaError_t launch_point_query_p61_sd(const QueryArgs& a, const u64* coef_host,
+                                      cudaStream_t stream);
 
 cudaError_t launch_add_counters(long long* dst, const long long* src, u64 n, cudaStream_t stream);
 

@@ -329,6 +329,26 @@ def test_point_query(env, b, c, mode):
     assert np.array_equal(got, oracle.point_query(b, c, k, mode, coeffs, C, q))
 
 
+@pytest.mark.parametrize("t,k,mode", [(7, 4, 0), (7, 4, 1), (5, 4, 1), (3, 4, 0), (5, 2, 0)])
+def test_point_query_shapes_and_edge_keys(env, t, k, mode):
+    """2^61-1 point queries: the signed-digit kernel (k = 4, t = 5 or 7) and the
+    generic one (other t and k), with keys at and above p (the hash depends on
+    x mod p) among ragged numbers of queries."""
+    torch, ms = env
+    n, m, seed = 30011, 1 << 12, 41 + t + k
+    keys = datagen.zipf(37 + t, 1.1, 1 << 20, n)
+    p = (1 << 61) - 1
+    edge = np.array([0, 1, p - 1, p, p + 1, (1 << 64) - 1, (1 << 63) + 5], dtype=np.uint64)
+    keys = np.concatenate([keys, edge, edge])
+    sk = ms.Sketch(t=t, m=m, k=k, seed=seed, mode=mode)
+    sk.update(to_dev(torch, keys))
+    coeffs = oracle.sketch_coeffs(61, 1, k, t, mode, seed)
+    C = oracle.cs_update(61, 1, k, t, m, mode, coeffs, keys)
+    for q in (np.concatenate([edge, keys[:1000]]), keys[:1], keys[-3:]):
+        got = sk.point_query(to_dev(torch, q)).cpu().numpy()
+        assert np.array_equal(got, oracle.point_query(61, 1, k, mode, coeffs, C, q))
+
+
 def test_many_sketches_same_stream_differ_only_by_seed(env):
     torch, ms = env
     keys = make_keys(61, 1, 5000, 1)
