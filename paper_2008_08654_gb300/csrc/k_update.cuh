@@ -977,12 +977,43 @@ __global__ void __launch_bounds__(256) k_gtable_drain_sd(const UpdateArgs a,
 
 // ------------------------------------------------------------ point queries
 //
+// The median of t = 5 or 7 estimates by a comparator network: Batcher's
+// odd-even merge sort on 8 wires, the wires past t fixed at +infinity (their
+// comparators drop out), pruned to the comparators the middle wire depends on,
+// and where only one output of a comparator is used, only that min (lo, on
+// the first wire) or max (hi, on the second).  A min/max network selects the
+// middle value of every input iff it does so on every 0/1 input;
+// tests/test_median_networks.py checks that on the networks as written here.
+__device__ __forceinline__ void med_ce(long long& x, long long& y) {
+    const long long a = x < y ? x : y;
+    y = x < y ? y : x;
+    x = a;
+}
+__device__ __forceinline__ void med_lo(long long& x, long long y) { x = x < y ? x : y; }
+__device__ __forceinline__ void med_hi(long long x, long long& y) { y = x < y ? y : x; }
+
+__device__ __forceinline__ long long median_of(long long (&e)[5]) {
+    // median network, t = 5
+    med_ce(e[0], e[1]); med_ce(e[2], e[3]); med_ce(e[0], e[2]); med_lo(e[1], e[3]);
+    med_ce(e[1], e[2]); med_hi(e[0], e[4]); med_lo(e[2], e[4]); med_hi(e[1], e[2]);
+    return e[2];
+}
+
+__device__ __forceinline__ long long median_of(long long (&e)[7]) {
+    // median network, t = 7
+    med_ce(e[0], e[1]); med_ce(e[2], e[3]); med_ce(e[4], e[5]); med_ce(e[0], e[2]);
+    med_ce(e[1], e[3]); med_ce(e[4], e[6]); med_ce(e[1], e[2]); med_ce(e[5], e[6]);
+    med_hi(e[0], e[4]); med_hi(e[1], e[5]); med_lo(e[2], e[6]); med_hi(e[2], e[4]);
+    med_lo(e[3], e[5]); med_lo(e[3], e[4]);
+    return e[3];
+}
+//
 // Point queries for p = 2^61-1, k = 4 and compile-time t: the estimate of f_x
 // is the median over the rows of s_r(x) C[r][i_r(x)] (Sec. 1.3).  Each key's
 // rows by the update kernels' signed-digit power sum (x^2, x^3 once per key,
 // the coefficients in the parameter space), the split of the sketch's mode
 // (ANY: Algorithm Mersenne-arb-r as in the lean kernel), the t estimates in
-// registers, and their median as the estimate of rank t/2 (ties broken by row).
+// registers, and their median by the network above.
 template <int T, int NF, bool ANY>
 __global__ void __launch_bounds__(256) k_cs_point_query_sd(const QueryArgs a,
                                                             const ParamCoef<msf::P61, NF * T, 4> pc) {
@@ -1018,16 +1049,7 @@ __global__ void __launch_bounds__(256) k_cs_point_query_sd(const QueryArgs a,
             const long long c = __ldg(a.counters + ((u64)r << log2m) + bucket);
             est[r] = neg ? -c : c;
         }
-        long long med = est[0];
-#pragma unroll
-        for (int i = 0; i < T; ++i) {
-            int rank = 0;
-#pragma unroll
-            for (int q = 0; q < T; ++q)
-                rank += (est[q] < est[i] || (est[q] == est[i] && q < i)) ? 1 : 0;
-            if (rank == T / 2) med = est[i];
-        }
-        a.out[j] = med;
+        a.out[j] = median_of(est);
     }
 }
 
