@@ -1171,4 +1171,84 @@ k_cs_update_tile(const UpdateArgs a,
     }
 }
 
+// The same lean kernel for p = 2^31-1, k = 4 (32-bit keys, four a thread by
+// one 16-byte load; the prime's power-sum rows, row_bs, with the coefficients
+// in the parameter space), power-of-two buckets.
+template <int T, int MODE, bool WEIGHTED, int LOG2M>
+__global__ void __launch_bounds__(512, (MODE != CS_TWO_POLY && T == 5) ? 3 : 2)
+k_cs_update_tile31(const UpdateArgs a,
+                   const ParamCoef<msf::P31, (MODE == CS_TWO_POLY ? 2 : 1) * T, 4> pc) {
+    typedef msf::P31 F;
+    constexpr int NF = (MODE == CS_TWO_POLY) ? 2 : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* tile = reinterpret_cast<int*>(smem);
+    const int log2m = LOG2M > 0 ? LOG2M : a.log2m;
+    const u32 mask = (1u << log2m) - 1u;
+    const u32 row_bytes = 4u << log2m;
+    const u32 cells = (u32)T << log2m;
+    for (u32 i = threadIdx.x; i < cells; i += blockDim.x) tile[i] = 0;
+    __syncthreads();
+    const u32 base = (u32)__cvta_generic_to_shared(tile);
+    const u64 n = a.n;
+    const u32 w_safe = a.w_safe;
+    const bool vec = a.vec_ok != 0;
+    const u32* keys = reinterpret_cast<const u32*>(a.keys);
+    const u64 groups = (n + 3) / 4;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += stride) {
+        const u64 j = 4 * g;
+        u32 key[4];
+        int wt[4];
+        if (vec && j + 3 < n) {
+            const uint4 k4 = __ldcs(reinterpret_cast<const uint4*>(keys + j));
+            key[0] = k4.x; key[1] = k4.y; key[2] = k4.z; key[3] = k4.w;
+            if (WEIGHTED) {
+                const int4 w4 = __ldcs(reinterpret_cast<const int4*>(a.weights + j));
+                wt[0] = w4.x; wt[1] = w4.y; wt[2] = w4.z; wt[3] = w4.w;
+            } else {
+                wt[0] = wt[1] = wt[2] = wt[3] = 1;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {  // past the end: key 0 with weight 0 (adds nothing)
+                const bool in = j + q < n;
+                key[q] = in ? __ldcs(keys + j + q) : 0u;
+                wt[q] = in ? (WEIGHTED ? __ldcs(a.weights + j + q) : 1) : 0;
+            }
+        }
+#pragma unroll(WEIGHTED ? 4 : 1)
+        for (int q = 0; q < 4; ++q) {
+            const u32 kq = key[0];
+            const int w = wt[0];
+            key[0] = key[1];
+            key[1] = key[2];
+            key[2] = key[3];
+            wt[0] = wt[1];
+            wt[1] = wt[2];
+            wt[2] = wt[3];
+            if (WEIGHTED && (u32)w + w_safe > 2u * w_safe) {  // |w| > w_safe (w_safe < 2^31)
+                update_big_key<F, NF>(FieldOps<F>::prep(kq), w, a.coef_dev, T, 4, log2m, 0u,
+                                      a.counters);
+                continue;
+            }
+            F::Pow3 xp;
+            F::powers3(kq, xp);
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                u32 bucket, sb;
+                ps_row_bs<F, NF>(xp, pc, r, mask, bucket, sb);
+                const int d = sb ? -w : w;
+                asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(base + (u32)r * row_bytes + (bucket << 2)),
+                             "r"(d)
+                             : "memory");
+            }
+        }
+    }
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < cells; i += blockDim.x) {
+        const int v = tile[i];
+        if (v != 0) global_add64(a.counters + i, (long long)v);
+    }
+}
+
 }  // namespace msk

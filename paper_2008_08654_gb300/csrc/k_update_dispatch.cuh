@@ -78,6 +78,19 @@ static cudaError_t launch_exact(const UpdateArgs& a, const u64* coef_host, const
             kern = a.weights ? k_cs_update_tile<T, MODE, true, 0, true>
                              : k_cs_update_tile<T, MODE, false, 0, true>;
     }
+    if constexpr (std::is_same<F, msf::P31>::value && T > 0 && K == 4 && PLACE == PLACE_SMEM &&
+                  STRAT == STRAT_POWER_SUM) {
+        if (update_uses_lean_tile(PRIME_31, a, cfg.place, cfg.strategy)) {
+            if (a.weights)
+                kern = a.log2m == 10   ? k_cs_update_tile31<T, MODE, true, 10>
+                       : a.log2m == 12 ? k_cs_update_tile31<T, MODE, true, 12>
+                                       : k_cs_update_tile31<T, MODE, true, 0>;
+            else
+                kern = a.log2m == 10   ? k_cs_update_tile31<T, MODE, false, 10>
+                       : a.log2m == 12 ? k_cs_update_tile31<T, MODE, false, 12>
+                                       : k_cs_update_tile31<T, MODE, false, 0>;
+        }
+    }
     if constexpr (std::is_same<F, msf::P61>::value && T > 0 && K == 4 && PLACE == PLACE_SMEM &&
                   STRAT == STRAT_POWER_SUM) {
         if (update_uses_lean_tile(PRIME_61, a, cfg.place, cfg.strategy)) {

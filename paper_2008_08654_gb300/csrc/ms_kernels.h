@@ -73,13 +73,14 @@ inline bool update_is_specialized(int prime, int t, int k, u32 arb_r) {
     return k == 4 && (t == 5 || t == 7) && (arb_r == 0 || prime == PRIME_61);
 }
 
-// Whether a specialized 2^61-1 update with a shared-memory tile runs the lean
-// one-key-a-thread kernel (k_cs_update_tile) rather than the general one:
-// power-of-two or any number of buckets, no statistics hook, no request for
-// the general kernel.
+// Whether a specialized update with a shared-memory tile runs a lean
+// one-key-a-thread kernel rather than the general one: 2^61-1 (k_cs_update_tile,
+// power-of-two or any number of buckets) or 2^31-1 (k_cs_update_tile31,
+// power-of-two buckets), no statistics hook, no request for the general kernel.
 inline bool update_uses_lean_tile(int prime, const UpdateArgs& a, int place, int strategy) {
-    return prime == PRIME_61 && a.k == 4 && (a.t == 5 || a.t == 7) && place == PLACE_SMEM &&
-           strategy == STRAT_POWER_SUM && a.hashed == nullptr && a.keys_per_thread_hint == 0;
+    return (prime == PRIME_61 || (prime == PRIME_31 && a.arb_r == 0)) && a.k == 4 &&
+           (a.t == 5 || a.t == 7) && place == PLACE_SMEM && strategy == STRAT_POWER_SUM &&
+           a.hashed == nullptr && a.keys_per_thread_hint == 0;
 }
 
 // Second-level key table: hashes every key it holds with its count into the
