@@ -1012,7 +1012,7 @@ __device__ __forceinline__ long long median_of(long long (&e)[7]) {
 // is the median over the rows of s_r(x) C[r][i_r(x)] (Sec. 1.3).  Each key's
 // rows by the update kernels' signed-digit power sum (x^2, x^3 once per key,
 // the coefficients in the parameter space), the split of the sketch's mode
-// (ANY: Algorithm Mersenne-arb-r as in the lean kernel), the t estimates in
+// (ANY: Algorithm Mersenne-arb-r, P61::arb_split_sd), the t estimates in
 // registers, and their median by the network above.
 template <int T, int NF, bool ANY>
 __global__ void __launch_bounds__(256) k_cs_point_query_sd(const QueryArgs a,
@@ -1033,10 +1033,9 @@ __global__ void __launch_bounds__(256) k_cs_point_query_sd(const QueryArgs a,
                       pc.k1[NF * r], pc.c2p31, ylo, yhi);
             u32 bucket, neg;
             if constexpr (ANY) {
-                const u32 hlo = ylo + 1u;  // h + 1 = (hhi : hlo), h < 2^61 - 1
-                const u32 hhi = (yhi & 0x1FFFFFFFu) + (hlo == 0u ? 1u : 0u);
-                bucket = (u32)(((u64)(hhi & 0x0FFFFFFFu) * a.arb_r + __umulhi(hlo, a.arb_r)) >> 28);
-                neg = (hhi >> 28) ^ 1u;  // subtract when a = 0
+                u32 keep;
+                F::arb_split_sd(ylo, yhi, a.arb_r, bucket, keep);
+                neg = keep ^ 1u;  // subtract when a = 0
             } else {
                 bucket = ylo & mask;
                 neg = (yhi >> 28) & 1u;  // bit 60 of the residue
@@ -1070,12 +1069,9 @@ __global__ void __launch_bounds__(256) k_cs_point_query_sd(const QueryArgs a,
 // (three 512-thread blocks per SM), the others at 64.  With unit weights the
 // four keys go through a rolled loop (their registers rotate): unrolled, the
 // compiler interleaves them and spills.  ANY: any number of buckets r
-// (Algorithm Mersenne-arb-r, Sec. 3.3) in rows 2^log2m >= r wide: with h the
-// canonical residue and h + 1 = a 2^60 + j (j < 2^60), the bucket is
-// floor(r j / 2^60) -- taken here from j's 28- and 32-bit halves as
-// floor((j_hi r + floor(j_lo r / 2^32)) / 2^28), the same integer -- and the
-// update is subtracted when a = 0 (two polynomials: the sign is still bit 60
-// of the second one).
+// (Algorithm Mersenne-arb-r, Sec. 3.3, P61::arb_split_sd) in rows 2^log2m >= r
+// wide, the update subtracted when a = 0 (two polynomials: the sign is still
+// bit 60 of the second one).
 template <int T, int MODE, bool WEIGHTED, int LOG2M, bool ANY = false>
 __global__ void __launch_bounds__(512, (MODE != CS_TWO_POLY && T == 5) ? 3 : 2)
 k_cs_update_tile(const UpdateArgs a,
@@ -1143,10 +1139,7 @@ k_cs_update_tile(const UpdateArgs a,
                           pc.k1[NF * r], pc.c2p31, ylo, yhi);
                 u32 bucket, keep = 0;
                 if constexpr (ANY) {
-                    const u32 hlo = ylo + 1u;  // h + 1 = (hhi : hlo), h < 2^61 - 1
-                    const u32 hhi = (yhi & 0x1FFFFFFFu) + (hlo == 0u ? 1u : 0u);
-                    bucket = (u32)(((u64)(hhi & 0x0FFFFFFFu) * a.arb_r + __umulhi(hlo, a.arb_r)) >> 28);
-                    keep = hhi >> 28;  // a: add when 1, subtract when 0
+                    F::arb_split_sd(ylo, yhi, a.arb_r, bucket, keep);  // add when a = 1
                 } else {
                     bucket = ylo & mask;
                 }

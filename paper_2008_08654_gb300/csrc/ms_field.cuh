@@ -247,6 +247,19 @@ struct P61 {
         return ((u64)(yhi & 0x1FFFFFFFu) << 32) | ylo;
     }
 
+    // Algorithm Mersenne-arb-r (Sec. 3.3) on row_sd's output: with h the
+    // canonical residue and h + 1 = a 2^60 + j (j < 2^60), the bucket is
+    // floor(r j / 2^60) -- taken from j's 28- and 32-bit halves as
+    // floor((j_hi r + floor(j_lo r / 2^32)) / 2^28), the same integer -- and a
+    // is returned (the update is subtracted when a = 0).
+    __device__ static __forceinline__ void arb_split_sd(u32 ylo, u32 yhi, u32 r, u32& bucket,
+                                                        u32& a) {
+        const u32 hlo = ylo + 1u;  // h + 1 = (hhi : hlo), h < 2^61 - 1
+        const u32 hhi = (yhi & 0x1FFFFFFFu) + (hlo == 0u ? 1u : 0u);
+        bucket = (u32)(((u64)(hhi & 0x0FFFFFFFu) * r + __umulhi(hlo, r)) >> 28);
+        a = hhi >> 28;
+    }
+
     // Bucket (low bits) and sign bit (bit 60) of the canonical residue.
     __device__ static __forceinline__ void bucket_sign_sd(u32 ylo, u32 yhi, u32 mask, u32& bucket,
                                                           u32& sign) {

@@ -414,3 +414,33 @@ def test_p61_rows_onto_p_and_at_digit_extremes():
             xs.append(X)
         y = p61_row(xs, a) & P61
         assert y == (a[0] + sum(a[i + 1] * xs[i] for i in range(3))) % P61
+
+
+def test_p61_arb_split_from_row_words():
+    """P61::arb_split_sd: the any-m bucket floor(r j / 2^60) of h + 1 = a 2^60 + j
+    (Algorithm Mersenne-arb-r, Sec. 3.3), taken from row_sd's two output words
+    as floor((j_hi r + floor(j_lo r / 2^32)) / 2^28) with j = j_hi 2^32 + j_lo,
+    and a = bit 60 of h + 1: emulated in 32/64-bit words against the definition
+    at the extremes of h and r and on random values."""
+    import random
+    rng = random.Random(3)
+    P = (1 << 61) - 1
+    hs = [0, 1, P - 1, P - 2, (1 << 60) - 1, 1 << 60, (1 << 60) - 2, (1 << 32) - 1, 1 << 32]
+    hs += [rng.randrange(P) for _ in range(2000)]
+    rs = [1, 2, 3, 1000, (1 << 24) - 1, 1 << 24, (1 << 32) - 1] + [rng.randrange(1, 1 << 32) for _ in range(20)]
+    for h in hs:
+        # row_sd's output words: canonical h in (yhi mod 2^29 : ylo); the bits above
+        # are whatever the lazy sum left there (the helper masks them off)
+        ylo = h & 0xFFFFFFFF
+        yhi = (h >> 32) | (rng.randrange(8) << 29)
+        hlo = (ylo + 1) & 0xFFFFFFFF
+        hhi = (yhi & 0x1FFFFFFF) + (1 if hlo == 0 else 0)
+        a = hhi >> 28
+        hx = h + 1
+        assert a == hx >> 60
+        j = hx & ((1 << 60) - 1)
+        for r in rs:
+            umulhi = (hlo * r) >> 32
+            wide = ((hhi & 0x0FFFFFFF) * r + umulhi) & ((1 << 64) - 1)
+            assert (hhi & 0x0FFFFFFF) * r + umulhi < 1 << 64
+            assert wide >> 28 == (r * j) >> 60, (h, r)
