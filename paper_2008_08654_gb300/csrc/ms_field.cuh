@@ -342,6 +342,18 @@ struct P89 {
     typedef u128x key_t;
     typedef u128x val_t;
 
+    // The 32x32->64 multiply-adds of this prime's limb arithmetic as plain C++
+    // (they shadow the inline-PTX madw / madws inside this struct): on the
+    // 2^30-key sweep the compiler's own scheduling of these rows was 6% faster
+    // (22.6 vs 24.1 ms), while the other primes' rows are faster with the PTX
+    // form.
+    __device__ static __forceinline__ u64 madw(u32 a, u32 b, u64 c) {
+        return (u64)a * (u64)b + c;
+    }
+    __device__ static __forceinline__ u64 madws(int a, int b, u64 c) {
+        return (u64)((long long)a * (long long)b) + c;
+    }
+
     __device__ static __forceinline__ u128 Pv() { return (((u128)1) << 89) - 1; }
 
     __device__ static __forceinline__ u128 load(const u128x& v) {
