@@ -1244,4 +1244,68 @@ k_cs_update_tile31(const UpdateArgs a,
     }
 }
 
+// The lean kernel for the wider primes' power sum (p = 2^89-1 and 2^64-59,
+// k = 4, power-of-two buckets): the keys of a four-key group through the
+// prime's key loader, then one key at a time (a rolled loop, the registers
+// rotating) through x^2, x^3 and the rows (ps_row_bs), the coefficients in the
+// parameter space.
+template <class F, int T, int MODE, bool WEIGHTED, int LOG2M>
+__global__ void __launch_bounds__(512, 2)
+k_cs_update_tile_ps(const UpdateArgs a, const ParamCoef<F, (MODE == CS_TWO_POLY ? 2 : 1) * T, 4> pc) {
+    typedef FieldOps<F> Ops;
+    constexpr int NF = (MODE == CS_TWO_POLY) ? 2 : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* tile = reinterpret_cast<int*>(smem);
+    const int log2m = LOG2M > 0 ? LOG2M : a.log2m;
+    const u32 mask = (1u << log2m) - 1u;
+    const u32 row_bytes = 4u << log2m;
+    const u32 cells = (u32)T << log2m;
+    for (u32 i = threadIdx.x; i < cells; i += blockDim.x) tile[i] = 0;
+    __syncthreads();
+    const u32 base = (u32)__cvta_generic_to_shared(tile);
+    const u64 n = a.n;
+    const u32 w_safe = a.w_safe;
+    const bool vec = a.vec_ok != 0;
+    const u64 groups = (n + 3) / 4;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += stride) {
+        const u64 j = 4 * g;
+        typename Ops::key_t key[4];
+        int wt[4];
+        KeyIO<F>::load(a.keys, j, n, vec, key);
+        load_weights4(WEIGHTED ? a.weights : nullptr, j, n, vec, wt);
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const typename Ops::key_t kq = key[0];
+            const int w = wt[0];
+            key[0] = key[1];
+            key[1] = key[2];
+            key[2] = key[3];
+            wt[0] = wt[1];
+            wt[1] = wt[2];
+            wt[2] = wt[3];
+            if (WEIGHTED && (u32)w + w_safe > 2u * w_safe) {  // |w| > w_safe (w_safe < 2^31)
+                update_big_key<F, NF>(Ops::prep(kq), w, a.coef_dev, T, 4, log2m, 0u, a.counters);
+                continue;
+            }
+            typename F::Pow3 xp;
+            F::powers3(kq, xp);
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                u32 bucket, sb;
+                ps_row_bs<F, NF>(xp, pc, r, mask, bucket, sb);
+                const int d = sb ? -w : w;
+                asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(base + (u32)r * row_bytes + (bucket << 2)),
+                             "r"(d)
+                             : "memory");
+            }
+        }
+    }
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < cells; i += blockDim.x) {
+        const int v = tile[i];
+        if (v != 0) global_add64(a.counters + i, (long long)v);
+    }
+}
+
 }  // namespace msk

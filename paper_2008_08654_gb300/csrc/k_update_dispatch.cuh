@@ -91,6 +91,20 @@ static cudaError_t launch_exact(const UpdateArgs& a, const u64* coef_host, const
                                        : k_cs_update_tile31<T, MODE, false, 0>;
         }
     }
+    if constexpr ((std::is_same<F, msf::P89>::value || std::is_same<F, msf::P64>::value) && T > 0 &&
+                  K == 4 && PLACE == PLACE_SMEM && STRAT == STRAT_POWER_SUM) {
+        constexpr int PR = std::is_same<F, msf::P89>::value ? PRIME_89 : PRIME_64_59;
+        if (update_uses_lean_tile(PR, a, cfg.place, cfg.strategy)) {
+            if (a.weights)
+                kern = a.log2m == 10   ? k_cs_update_tile_ps<F, T, MODE, true, 10>
+                       : a.log2m == 12 ? k_cs_update_tile_ps<F, T, MODE, true, 12>
+                                       : k_cs_update_tile_ps<F, T, MODE, true, 0>;
+            else
+                kern = a.log2m == 10   ? k_cs_update_tile_ps<F, T, MODE, false, 10>
+                       : a.log2m == 12 ? k_cs_update_tile_ps<F, T, MODE, false, 12>
+                                       : k_cs_update_tile_ps<F, T, MODE, false, 0>;
+        }
+    }
     if constexpr (std::is_same<F, msf::P61>::value && T > 0 && K == 4 && PLACE == PLACE_SMEM &&
                   STRAT == STRAT_POWER_SUM) {
         if (update_uses_lean_tile(PRIME_61, a, cfg.place, cfg.strategy)) {

@@ -75,10 +75,11 @@ inline bool update_is_specialized(int prime, int t, int k, u32 arb_r) {
 
 // Whether a specialized update with a shared-memory tile runs a lean
 // one-key-a-thread kernel rather than the general one: 2^61-1 (k_cs_update_tile,
-// power-of-two or any number of buckets) or 2^31-1 (k_cs_update_tile31,
-// power-of-two buckets), no statistics hook, no request for the general kernel.
+// power-of-two or any number of buckets), 2^31-1 (k_cs_update_tile31) and the
+// wider primes (k_cs_update_tile_ps) with power-of-two buckets; no statistics
+// hook, no request for the general kernel.
 inline bool update_uses_lean_tile(int prime, const UpdateArgs& a, int place, int strategy) {
-    return (prime == PRIME_61 || (prime == PRIME_31 && a.arb_r == 0)) && a.k == 4 &&
+    return (prime == PRIME_61 || a.arb_r == 0) && a.k == 4 &&
            (a.t == 5 || a.t == 7) && place == PLACE_SMEM && strategy == STRAT_POWER_SUM &&
            a.hashed == nullptr && a.keys_per_thread_hint == 0;
 }

@@ -38,8 +38,8 @@ def test_power_sum_every_placement(env, b, c, t, mode, place):
     sk, C, f2, rows = run_sketch(torch, ms, b, c, t, m, 4, mode, keys, w, seed, place=place,
                                  strategy=1)
     ll = sk.last_launch()
-    # 2^31-1 with a shared-memory tile runs the lean kernel (specialized == 2)
-    lean = b == 31 and place == 0
+    # a shared-memory tile runs the lean kernels (specialized == 2)
+    lean = place == 0
     assert ll["place"] == place and ll["strategy"] == 1 and ll["specialized"] == (2 if lean else 1), ll
     check_sketch(sk, C, f2, rows, b, c, 4, mode, keys, w, seed)
 
