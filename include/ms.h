@@ -335,9 +335,10 @@ ms_status cs_import(cs_sketch** out, const void* buf_host, size_t size);
  *  strategy: 0 = Horner per row (Algorithm Mersenne), 1 = powers of x once per
  *            key, then sum a_i x^i per row (k = 4 with t = 5 or 7, every prime;
  *            for the other primes only with a power-of-two m; other sketches
- *            use Horner); 2 = the power sum as 1, but for 2^61-1 with a
- *            shared-memory tile in the general kernel (four keys a thread)
- *            instead of the lean one (one key a thread; the default there).
+ *            use Horner); 2 = the power sum as 1, but with a shared-memory
+ *            tile in the general kernel (four keys a thread) instead of the
+ *            lean one (one key a thread; the default there for every prime
+ *            with a power-of-two m, and for 2^61-1 with any m).
  *            All give identical hash values.
  *  threads (multiple of 32, <= 512; default 512, 256 for place 1; the lean
  *  kernel on a stream of two or three rounds of four keys a thread takes one
